@@ -1,0 +1,302 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Every check below is chosen so that a plausible slip in the oracle (a dropped factor, a wrong
+exchange sign, a transposed operand) fails at least one of them; test_planted_mistakes plants
+such slips and confirms that they are caught.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+from las_inputs import config_system, make_system, splitmix64
+from las_inputs.rdm import fragment_rdms, nstrings, strings
+from oracle import las_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def cfg0():
+    return config_system(0)
+
+
+@pytest.fixture(scope="module")
+def small3():
+    # three fragments of different size, one with an odd electron count (Ms = 1/2)
+    return make_system(14, 40, 3, [(2, 2), (3, 3), (2, 3)], seed=777)
+
+
+def test_splitmix64_golden():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "splitmix64.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    gamma = np.uint64(0x9E3779B97F4A7C15)
+    for i, ref in rows:
+        got = int(splitmix64(np.array([int(i)], dtype=np.uint64) * gamma)[0])
+        assert got == int(ref, 16)
+
+
+def test_generator_properties(cfg0):
+    s = cfg0
+    assert np.abs(s.C.T @ s.C - np.eye(s.nmo)).max() < 1e-13
+    assert np.allclose(s.h, s.h.T)
+    # B decays along L as exp(-L/Naux): compare mean squares of first and last quarters
+    q = s.naux // 4
+    r = np.mean(s.Bp[-q:] ** 2) / np.mean(s.Bp[:q] ** 2)
+    expect = np.mean(np.exp(-2 * np.arange(s.naux - q, s.naux) / s.naux)) / np.mean(
+        np.exp(-2 * np.arange(q) / s.naux))
+    assert abs(r / expect - 1) < 0.1
+
+
+def test_rdm_sum_rules():
+    for ne, m in [(2, 2), (4, 4), (6, 8), (3, 3), (6, 6)]:
+        from las_inputs.gen import ci_vector
+        ci = ci_vector(99, 0, m, ne)
+        g1, g2 = fragment_rdms(ci, m, ne)
+        na, nb = ne // 2, ne - ne // 2
+        assert abs(np.trace(g1[0]) - na) < 1e-12
+        assert abs(np.trace(g1[1]) - nb) < 1e-12
+        D = g1[0] + g1[1]
+        assert np.abs(np.einsum("pqrr->pq", g2) - (ne - 1) * D).max() < 1e-12
+        assert np.abs(g2 - g2.transpose(2, 3, 0, 1)).max() < 1e-12      # pair swap
+        assert np.abs(g2 - g2.transpose(1, 0, 3, 2)).max() < 1e-12      # hermiticity (real)
+        w = np.linalg.eigvalsh(D)
+        assert w.min() > -1e-12 and w.max() < 2 + 1e-12
+        assert abs(np.einsum("pprr->", g2) - ne * (ne - 1)) < 1e-10
+
+
+def test_rdm_one_hot_determinant():
+    m, ne = 4, 4
+    na = nb = 2
+    sa, sb = strings(m, na), strings(m, nb)
+    ci = np.zeros((nstrings(m, na), nstrings(m, nb)))
+    ia, ib = 2, 4
+    ci[ia, ib] = 1.0
+    g1, g2 = fragment_rdms(ci, m, ne)
+    occa = np.array([(sa[ia] >> k) & 1 for k in range(m)], float)
+    occb = np.array([(sb[ib] >> k) & 1 for k in range(m)], float)
+    assert np.allclose(g1[0], np.diag(occa)) and np.allclose(g1[1], np.diag(occb))
+    # single determinant: Gamma_pqrs = d_pq d_rs n_p n_r - d_ps d_qr sum_s n_ps n_qs
+    n = occa + occb
+    I = np.eye(m)
+    ref = np.einsum("pq,rs,p,r->pqrs", I, I, n, n) - np.einsum(
+        "ps,qr,pq->pqrs", I, I, np.outer(occa, occa) + np.outer(occb, occb))
+    assert np.abs(g2 - ref).max() < 1e-14
+
+
+def test_df_jk_brute_force():
+    s = make_system(10, 30, 2, [(2, 2)], seed=5)
+    n = s.nao
+    eri = O.ao_eri(s.Bp, n)
+    rng = np.random.default_rng(0)
+    D = rng.standard_normal((n, n))
+    D = D + D.T
+    (J,), (K,) = O.df_jk(s.Bp, n, [D])
+    assert np.abs(J - np.einsum("mnls,ls->mn", eri, D)).max() < 1e-12
+    assert np.abs(K - np.einsum("mlsn,ls->mn", eri, D)).max() < 1e-12
+    # 8-fold symmetry of the AO integrals built from the factorisation
+    for perm in [(1, 0, 2, 3), (0, 1, 3, 2), (2, 3, 0, 1), (3, 2, 1, 0)]:
+        assert np.abs(eri - eri.transpose(perm)).max() < 1e-13
+
+
+def test_active_integral_symmetry(cfg0):
+    s = cfg0
+    a = s.nactive
+    C_a = s.C[:, s.ncore:s.ncore + a]
+    eri, mveri = O.ao2mo_active(s.Bp, s.nao, C_a)
+    for perm in [(1, 0, 2, 3), (0, 1, 3, 2), (2, 3, 0, 1), (1, 0, 3, 2), (3, 2, 1, 0)]:
+        assert np.abs(eri - eri.transpose(perm)).max() < 1e-12
+    # (mu v|wx) projected with C_a gives (uv|wx); (pu|vw) has its 4-fold symmetry in (v,w)
+    assert np.abs(np.einsum("mu,mvwx->uvwx", C_a, mveri) - eri).max() < 1e-12
+    assert np.abs(mveri - mveri.transpose(0, 1, 3, 2)).max() < 1e-12
+    # the same integrals straight from the full MO brute force
+    full = O.mo_eri(s.Bp, s.nao, C_a)
+    assert np.abs(full - eri).max() < 1e-12
+
+
+def test_df_transform_matches_mo_integrals(cfg0):
+    s = cfg0
+    a0, a1 = s.ncore, s.ncore + s.nactive
+    lmu, lpu = O.df_transform(s.Bp, s.nao, s.C, (a0, a1), 0, s.nmo)
+    b = O.unpack_block(s.Bp, s.nao)
+    assert np.abs(lmu - np.einsum("Pmn,nu->Pmu", b, s.C[:, a0:a1])).max() < 1e-12
+    # (pu|vw) = sum_L (L|pu)(L|vw) equals the brute-force MO integrals
+    pu_vw = np.einsum("Lpu,Lvw->puvw", lpu, lpu[:, a0:a1, :])
+    full = O.mo_eri(s.Bp, s.nao, s.C)
+    assert np.abs(pu_vw - full[:, a0:a1, a0:a1, a0:a1]).max() < 1e-11
+
+
+@pytest.mark.parametrize("which", ["cfg0", "small3"])
+def test_energy_three_ways(which, request):
+    s = request.getfixturevalue(which)
+    eb = O.system_energy_grad(s, with_grad=False)["E"]
+    ea = O.energy_tier_a(s.Bp, s.nao, s.h, s.C, s.ncore, s.dm1s, s.dm2)
+    esc = O.energy_slater_condon(s)
+    assert abs(ea - eb) < 1e-12 * max(1, abs(eb))
+    assert abs(esc - eb) < 1e-12 * max(1, abs(eb))
+
+
+def test_one_hot_ci_closed_form():
+    s = make_system(12, 36, 2, [(2, 2), (4, 3)], seed=31)
+    # replace CI vectors by single determinants and rebuild the RDMs
+    occ_sets = []
+    for K, (ne, m) in enumerate(zip(s.nelec, s.nact)):
+        na, nb = ne // 2, ne - ne // 2
+        ci = np.zeros((nstrings(m, na), nstrings(m, nb)))
+        ci[-1, 0] = 1.0
+        s.ci[K] = ci
+        s.dm1s[K], s.dm2[K] = fragment_rdms(ci, m, ne)
+        off = s.ncore + sum(s.nact[:K])
+        sa, sb = strings(m, na)[-1], strings(m, nb)[0]
+        occ_sets += [(off + k, 0) for k in range(m) if (sa >> k) & 1]
+        occ_sets += [(off + k, 1) for k in range(m) if (sb >> k) & 1]
+    occ_sets += [(i, sp) for i in range(s.ncore) for sp in (0, 1)]
+    a = s.nactive
+    Cocc = s.C[:, :s.ncore + a]
+    hmo = Cocc.T @ s.h @ Cocc
+    eri = O.mo_eri(s.Bp, s.nao, Cocc)
+    e = sum(hmo[i, i] for i, _ in occ_sets)
+    e += 0.5 * sum(eri[i, i, j, j] - (eri[i, j, j, i] if si == sj else 0.0)
+                   for i, si in occ_sets for j, sj in occ_sets)
+    eb = O.system_energy_grad(s, with_grad=False)["E"]
+    assert abs(e - eb) < 1e-12 * max(1, abs(e))
+
+
+def test_no_fragments_rhf():
+    s = make_system(16, 48, 4, [], seed=11)
+    r = O.system_energy_grad(s)
+    Cc = s.C[:, :4]
+    hmo = Cc.T @ s.h @ Cc
+    eri = O.mo_eri(s.Bp, s.nao, Cc)
+    e = 2 * np.trace(hmo) + 2 * np.einsum("iijj->", eri) - np.einsum("ijji->", eri)
+    assert abs(r["E"] - e) < 1e-12 * max(1, abs(e))
+    # core columns of dE/dC are 4 F^I C_core; F^I from the brute-force AO integrals
+    aoeri = O.ao_eri(s.Bp, s.nao)
+    Dc = 2 * Cc @ Cc.T
+    FI = s.h + np.einsum("mnls,ls->mn", aoeri, Dc) - 0.5 * np.einsum("mlsn,ls->mn", aoeri, Dc)
+    assert np.abs(r["G"][:, :4] - 4 * FI @ Cc).max() < 1e-11
+    assert np.abs(r["G"][:, 4:]).max() == 0.0
+
+
+def test_rotation_invariances(cfg0):
+    s = cfg0
+    base = O.system_energy_grad(s)
+    rng = np.random.default_rng(3)
+    c = s.ncore
+    # core-core rotation
+    U = np.eye(s.nmo)
+    U[:c, :c] = sl.expm((lambda x: x - x.T)(rng.standard_normal((c, c))))
+    e1 = O.energy_grad(s.Bp, s.nao, s.h, s.C @ U, c, s.dm1s, s.dm2, with_grad=False)["E"]
+    assert abs(e1 - base["E"]) < 1e-11 * abs(base["E"])
+    # rotation inside one fragment, RDMs co-rotated: phi'_p = sum_a phi_a V_ap, gamma' = V^T gamma V
+    m = s.nact[0]
+    V = sl.expm((lambda x: x - x.T)(rng.standard_normal((m, m))))
+    U = np.eye(s.nmo)
+    U[c:c + m, c:c + m] = V
+    d1 = [np.einsum("ap,bq,sab->spq", V, V, s.dm1s[0])] + s.dm1s[1:]
+    d2 = [np.einsum("ap,bq,cr,ds,abcd->pqrs", V, V, V, V, s.dm2[0])] + s.dm2[1:]
+    e2 = O.energy_grad(s.Bp, s.nao, s.h, s.C @ U, c, d1, d2, with_grad=False)["E"]
+    assert abs(e2 - base["E"]) < 1e-11 * abs(base["E"])
+    g = base["gorb"]
+    o = s.nocc
+    assert np.abs(g[:c, :c]).max() < 1e-11 * np.abs(g).max()
+    assert np.abs(g[o:, o:]).max() == 0.0
+    assert np.abs(g + g.T).max() == 0.0
+
+
+def test_positivity(cfg0):
+    s = cfg0
+    r = O.system_energy_grad(s, with_grad=False)
+    Dc = 2 * s.C[:, :s.ncore] @ s.C[:, :s.ncore].T
+    assert np.sum(Dc * r["J"]) >= 0
+    assert np.sum(Dc * r["K"]) >= 0
+    b = O.unpack_block(s.Bp, s.nao)
+    v = np.einsum("Pmn,mn->P", b, Dc)
+    assert abs(np.sum(Dc * r["J"]) - np.sum(v * v)) < 1e-10 * np.sum(v * v)
+
+
+def _fd_check(s, ndir, eps=1e-4, seed=0):
+    r = O.system_energy_grad(s)
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for _ in range(ndir):
+        X = rng.standard_normal((s.nmo, s.nmo))
+        X = X - X.T
+        X /= np.linalg.norm(X)
+        ep = O.energy_grad(s.Bp, s.nao, s.h, s.C @ sl.expm(eps * X), s.ncore, s.dm1s, s.dm2,
+                           with_grad=False)["E"]
+        em = O.energy_grad(s.Bp, s.nao, s.h, s.C @ sl.expm(-eps * X), s.ncore, s.dm1s, s.dm2,
+                           with_grad=False)["E"]
+        an = float(np.sum((s.C.T @ r["G"]) * X))
+        worst = max(worst, abs((ep - em) / (2 * eps) - an) / max(1.0, abs(an)))
+    return worst
+
+
+def test_finite_differences(cfg0):
+    assert _fd_check(cfg0, 20) < 1e-6
+
+
+def test_finite_differences_odd_fragment(small3):
+    assert _fd_check(small3, 6) < 1e-6
+
+
+def test_planted_mistakes(cfg0, monkeypatch):
+    """Each planted slip in the oracle must be caught by one of the pins above."""
+    s = cfg0
+    good = O.system_energy_grad(s, with_grad=False)["E"]
+    esc = O.energy_slater_condon(s)
+    assert abs(good - esc) < 1e-10
+
+    # (1) wrong sign of the inter-fragment exchange block
+    orig = O.active_rdms
+
+    def bad_rdms(d1, d2):
+        D, G = orig(d1, d2)
+        m = d1[0].shape[-1]
+        G2 = G.copy()
+        G2[:m, m:, m:, :m] *= -1.0
+        G2[m:, :m, :m, m:] *= -1.0
+        return D, G2
+
+    monkeypatch.setattr(O, "active_rdms", bad_rdms)
+    assert abs(O.system_energy_grad(s, with_grad=False)["E"] - esc) > 1e-6
+    monkeypatch.setattr(O, "active_rdms", orig)
+
+    # (2) exchange of the core density without the factor 1/2
+    orig_jk = O.df_jk
+
+    def bad_jk(Bp, n, dms, l0=0, l1=None):
+        J, K = orig_jk(Bp, n, dms, l0, l1)
+        return J, [2 * k for k in K]
+
+    monkeypatch.setattr(O, "df_jk", bad_jk)
+    assert abs(O.system_energy_grad(s, with_grad=False)["E"] - esc) > 1e-6
+    monkeypatch.setattr(O, "df_jk", orig_jk)
+
+    # (3) a transposed C in the half transform of Eq. ao2mo_1
+    orig_ao = O.ao2mo_active
+
+    def bad_ao(Bp, n, C_a, l0=0, l1=None):
+        Ct = np.ascontiguousarray(np.roll(C_a, 1, axis=0))
+        return orig_ao(Bp, n, Ct, l0, l1)
+
+    monkeypatch.setattr(O, "ao2mo_active", bad_ao)
+    assert abs(O.system_energy_grad(s, with_grad=False)["E"] - esc) > 1e-6
+    monkeypatch.setattr(O, "ao2mo_active", orig_ao)
+
+    # (4) a dropped factor 2 in the active gradient columns must fail the FD pin
+    orig_eg = O.energy_grad
+
+    def bad_grad(*a, **k):
+        r = orig_eg(*a, **k)
+        if "G" in r:
+            c = a[4]
+            na = sum(d.shape[-1] for d in a[5])
+            r["G"][:, c:c + na] *= 0.5
+        return r
+
+    monkeypatch.setattr(O, "energy_grad", bad_grad)
+    assert _fd_check(s, 3) > 1e-3
+    monkeypatch.setattr(O, "energy_grad", orig_eg)
