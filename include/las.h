@@ -1,0 +1,136 @@
+/*
+ * las.h -- C ABI of the GB300 (sm_103a) library for the density-fitted LAS energy and its
+ * orbital gradient.
+ *
+ * Problem statement followed (arXiv 2505.03755):
+ *   - Cholesky / density-fitting factorisation of the two-electron integrals, Eq. cholesky:
+ *       g^{mu1 mu3}_{mu2 mu4} = b^P_{mu1 mu2} b^P_{mu3 mu4};
+ *     the vectors b^P are stored as packed lower triangles, Naux * Nao(Nao+1)/2 values
+ *     (section "Calculation of effective potentials").
+ *   - JK call, Eqs. J_1, J_2, K_1, K_2 (Coulomb and exchange matrices of a density).
+ *   - AO2MO, Eqs. ao2mo_1, ao2mo_2, ppaa (half and full transforms of b^P and the
+ *     (pp|aa)-type integrals).
+ *   - LAS wave function, Eq. las_wfn (fragment CAS states times a closed-shell core), its
+ *     energy E_LAS = <LAS|H|LAS>, and the orbital gradient whose vanishing is Eq. MO_conv.
+ *
+ * Conventions for every call:
+ *   - All arrays are FP64, row-major (C order), and all pointers are DEVICE pointers unless a
+ *     parameter says "host".  The caller owns every input and output buffer.
+ *   - MO columns of C are ordered: core [0, ncore), fragment 0, fragment 1, ..., virtuals.
+ *   - B_packed[L * nao(nao+1)/2 + mu(mu+1)/2 + nu] = b^L_{mu nu} for mu >= nu.
+ *   - Calls are asynchronous on the context's stream, except where stated.  A call returns
+ *     LAS_OK once its work is queued; errors found on the device (a failed bounds or status
+ *     check inside a kernel) are recorded in a status word and reported by the next
+ *     las_sync() (and by every later call).  The library never aborts and never traps.
+ *   - Nothing is allocated or freed inside a call other than las_create / las_destroy /
+ *     las_reserve.
+ *   - A context is not thread-safe: use one context per host thread, or serialise calls.
+ */
+#ifndef LAS_H_
+#define LAS_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct las_ctx las_ctx;
+
+typedef enum {
+  LAS_OK = 0,
+  LAS_ERR_ARG = 1,        /* invalid argument (sizes, partition, null pointer) */
+  LAS_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+  LAS_ERR_WORKSPACE = 3,  /* workspace cap too small for the smallest chunk */
+  LAS_ERR_TIMEOUT = 4,    /* a bounded device-side wait ran out */
+  LAS_ERR_INTERNAL = 5,   /* a device-side consistency check failed */
+  LAS_ERR_UNSUPPORTED = 6 /* valid request this build does not support (e.g. sizes too large) */
+} las_status;
+
+typedef enum {
+  LAS_FP64 = 0,       /* all contractions in native FP64 (DMMA) */
+  LAS_SPLIT_BF16 = 1  /* bulk contractions as split-precision (BF16 digit) GEMMs on tcgen05
+                         with exact FP32 partial sums recombined in integer arithmetic;
+                         reductions, traces and gradient assembly stay in FP64 */
+} las_precision;
+
+typedef struct {
+  int nao;          /* number of AOs n */
+  int naux;         /* number of auxiliary (Cholesky) vectors X */
+  int nmo;          /* number of MO columns of C, ncore + sum(nact) <= nmo <= nao */
+  int ncore;        /* doubly occupied core orbitals c */
+  int nfrag;        /* number of fragments (0 allowed: closed-shell core only) */
+  const int* nact;  /* host array [nfrag]: active orbitals per fragment, each >= 1 */
+} las_dims;
+
+/* Create a context over the packed Cholesky vectors B_packed (device, naux*nao(nao+1)/2
+ * doubles).  The context keeps a reference to B_packed (it must stay valid and unchanged until
+ * las_destroy); in LAS_SPLIT_BF16 mode it also builds, once, the digit planes of B it needs
+ * (owned by the context).  max_workspace_bytes caps the per-evaluation workspace (0 = choose);
+ * the auxiliary index is processed in chunks that fit it.  stream: a cudaStream_t (NULL = the
+ * legacy default stream).  Synchronous with respect to the set-up work. */
+las_status las_create(las_ctx** ctx, const las_dims* dims, const double* B_packed,
+                      las_precision precision, size_t max_workspace_bytes, void* stream);
+
+las_status las_destroy(las_ctx* ctx);
+
+/* Change the stream later calls are queued on. */
+las_status las_set_stream(las_ctx* ctx, void* stream);
+
+/* Wait for all queued work of this context; return the first recorded error, if any. */
+las_status las_sync(las_ctx* ctx);
+
+/* Bytes of device memory owned by the context (workspace + digit planes). */
+size_t las_device_bytes(const las_ctx* ctx);
+
+/* AO2MO half and full transforms (Eqs. ao2mo_1, ao2mo_2) over the active orbitals u:
+ *   Lmu_u[L][mu][u] = sum_nu b^L_{mu nu} C[nu][ncore+u]            (naux x nao x nact_total)
+ *   Lpu[L][p-p0][u] = sum_mu C[mu][p] Lmu_u[L][mu][u],  p in [p0,p1) (naux x (p1-p0) x nact_total)
+ * C: device [nao][nmo].  Either output may be NULL.  0 <= p0 <= p1 <= nmo. */
+las_status las_df_transform(las_ctx* ctx, const double* C, int p0, int p1, double* Lmu_u,
+                            double* Lpu);
+
+/* Coulomb and exchange matrices (Eqs. J_1-K_2) of the core density Dc = 2 C_core C_core^T:
+ *   J[mu][nu] = sum_L b^L_{mu nu} sum_{la,si} b^L_{la si} Dc[la][si]
+ *   K[mu][nu] = sum_L sum_{la,si} b^L_{mu la} Dc[la][si] b^L_{si nu}
+ * J, K: device [nao][nao]; either may be NULL. */
+las_status las_df_jk(las_ctx* ctx, const double* C, double* J, double* K);
+
+/* LAS energy.  h: device [nao][nao] one-electron Hamiltonian (symmetric).
+ * dm1s: device, per fragment K the spin-separated 1-RDM [2][m_K][m_K] (alpha, beta),
+ *       concatenated over fragments.
+ * dm2:  device, per fragment K the spin-summed 2-RDM [m_K]^4 in chemists' order,
+ *       Gamma[p][q][r][s] = sum_{s,t} <p+_s r+_t s_t q_s>, concatenated over fragments.
+ * E:    device pointer to one double (written asynchronously). */
+las_status las_energy(las_ctx* ctx, const double* C, const double* h, const double* dm1s,
+                      const double* dm2, double* E);
+
+/* LAS energy and its derivative with respect to the MO coefficients:
+ *   dEdC: device [nao][nmo], dE/dC[mu][p] (zero in the virtual columns);
+ *   gorb: device [nmo][nmo] or NULL, the antisymmetric orbital-rotation gradient
+ *         g = C^T dEdC - (C^T dEdC)^T, so that d/de E(C exp(e X))|_0 = sum_pq g[p][q] X[p][q] / 2
+ *         for antisymmetric X (equivalently sum_pq (C^T dEdC)[p][q] X[p][q]). */
+las_status las_energy_grad(las_ctx* ctx, const double* C, const double* h, const double* dm1s,
+                           const double* dm2, double* E, double* dEdC, double* gorb);
+
+/* The same evaluation with HOST inputs and outputs: C_host [nao][nmo], h_host [nao][nao],
+ * dm1s_host, dm2_host as above, E_host (1 double), dEdC_host [nao][nmo] (may be NULL).
+ * Copies in through context-owned device buffers, evaluates, copies back and synchronises.
+ * Host buffers may be pageable; page-locked buffers give overlapped, faster copies. */
+las_status las_energy_grad_host(las_ctx* ctx, const double* C_host, const double* h_host,
+                                const double* dm1s_host, const double* dm2_host,
+                                double* E_host, double* dEdC_host);
+
+/* Per-stage device times (milliseconds) of the last evaluation when timing is enabled with
+ * las_set_timing(ctx, 1); stage order: half transform, full transform, per-L contractions,
+ * projections, assembly.  Returns the number of stages written (<= cap). */
+las_status las_set_timing(las_ctx* ctx, int enable);
+int las_stage_times(las_ctx* ctx, float* ms, int cap);
+
+const char* las_status_str(las_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAS_H_ */

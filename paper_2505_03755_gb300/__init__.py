@@ -1,0 +1,10 @@
+"""GB300 (sm_103a) library for the density-fitted LAS energy and orbital gradient.
+
+The compute lives in liblasdf.so (C ABI declared in include/las.h); this package is its thin
+Python binding.  There is no CPU fallback.
+"""
+from .las import (EXPORTS, LAS_FP64, LAS_SPLIT_BF16, LasDF, LasError, las_energy,
+                  load_library)
+
+__all__ = ["EXPORTS", "LAS_FP64", "LAS_SPLIT_BF16", "LasDF", "LasError", "las_energy",
+           "load_library"]

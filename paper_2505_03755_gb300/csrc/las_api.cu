@@ -1,0 +1,483 @@
+// C ABI of liblasdf: context, validation, workspace plan and the evaluation chain.
+//
+// Evaluation chain for a chunk of auxiliary indices L (all FP64 in LAS_FP64 mode):
+//   S1  H_L  = b^L C_occ              half transform, Eq. ao2mo_1 (and the first GEMM of K_1)
+//   S2  T_L  = C_occ^T H_L            full transform over the occupied space, Eq. ao2mo_2
+//   S3/S4 per L: Coulomb vectors (Eq. J_1), Y_L = Gamma . T_L (the ppaa-type contraction with
+//       the block-product 2-RDM), the energy term eps_L and the projection matrix W_L
+//   S5/S6 Out += sum_L H_L W_L        (J_2 and K_2 projected on C_occ, and the active
+//                                      two-electron gradient)
+// then E = sum_L eps_L + one-electron terms, dE/dC = [4 h C_c | 2 h C_a D | 0] + Out, and
+// g = C^T dE/dC - transpose.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "gemm_f64.cuh"
+#include "las_common.cuh"
+#include "las_split.cuh"
+
+static thread_local char g_last_error[512];
+
+void las_record_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s failed: %s (%s:%d)", what,
+           cudaGetErrorString(e), file, line);
+}
+
+struct las_ctx {
+  int n, X, nmo, c, a, o, op;
+  long npair;
+  las_precision prec;
+  FragInfo fi;
+  FragInfo fi_c;  // core only (for the Coulomb vector of Dc)
+  const double* Bp;
+  cudaStream_t stream;
+  size_t ws_cap;
+  int Lc;       // auxiliary chunk length
+  int ksplit;   // split of the projection GEMM
+  // workspace (device)
+  double* Cocc;   // [n][op]
+  double* Ht;     // [Lc][op][n]
+  double* T;      // [Lc][op][op]
+  double* W;      // [Lc][op][op]
+  double* part;   // [ksplit][n][op]
+  double* Out;    // [n][op]
+  double* hC;     // [n][op]
+  double* hmo;    // [op][op]
+  double* M;      // [nmo][op]
+  double* eps;    // [X]
+  double* vc;     // [X]
+  double* va;     // [X]
+  double* Jp;     // [npair] (JK)
+  int* status;    // device status word
+  // staging for the host-buffer call
+  double *dC, *dh, *ddm1, *ddm2, *dE, *dG;
+  long ndm1, ndm2;
+  size_t bytes;
+  // split-precision state (owned)
+  SplitState* split;
+  // timing
+  int timing;
+  cudaEvent_t ev[8];
+  float stage_ms[8];
+  int nstage;
+};
+
+extern "C" const char* las_status_str(las_status s) {
+  switch (s) {
+    case LAS_OK: return "ok";
+    case LAS_ERR_ARG: return "invalid argument";
+    case LAS_ERR_CUDA: return g_last_error[0] ? g_last_error : "CUDA error";
+    case LAS_ERR_WORKSPACE: return "workspace cap too small";
+    case LAS_ERR_TIMEOUT: return "device-side wait timed out";
+    case LAS_ERR_INTERNAL: return "device-side consistency check failed";
+    case LAS_ERR_UNSUPPORTED: return "unsupported size or mode";
+  }
+  return "unknown status";
+}
+
+static las_status dalloc(las_ctx* x, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return LAS_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+    *p = nullptr;
+    return LAS_ERR_CUDA;
+  }
+  x->bytes += bytes;
+  return LAS_OK;
+}
+
+static void free_all(las_ctx* x) {
+  void* ptrs[] = {x->Cocc, x->Ht, x->T, x->W, x->part, x->Out, x->hC, x->hmo, x->M, x->eps,
+                  x->vc, x->va, x->Jp, x->status, x->dC, x->dh, x->ddm1, x->ddm2, x->dE, x->dG};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (x->split) split_destroy(x->split);
+  for (int i = 0; i < 8; ++i)
+    if (x->ev[i]) cudaEventDestroy(x->ev[i]);
+}
+
+static size_t chunk_bytes(const las_ctx* x, int Lc) {
+  size_t op = x->op, n = x->n;
+  return (size_t)Lc * op * (n + 2 * op) * sizeof(double);
+}
+
+extern "C" las_status las_create(las_ctx** out, const las_dims* d, const double* B_packed,
+                                 las_precision prec, size_t max_ws, void* stream) {
+  if (!out || !d || !B_packed) return LAS_ERR_ARG;
+  *out = nullptr;
+  if (d->nao <= 0 || d->naux <= 0 || d->nmo <= 0 || d->ncore < 0 || d->nfrag < 0) return LAS_ERR_ARG;
+  if (d->nfrag > LAS_MAX_FRAG || (d->nfrag > 0 && !d->nact)) return LAS_ERR_ARG;
+  if (prec != LAS_FP64 && prec != LAS_SPLIT_BF16) return LAS_ERR_ARG;
+  int a = 0;
+  for (int k = 0; k < d->nfrag; ++k) {
+    if (d->nact[k] < 1) return LAS_ERR_ARG;
+    a += d->nact[k];
+  }
+  if (d->ncore + a > d->nmo || d->nmo > d->nao) return LAS_ERR_ARG;
+  if (a > LAS_MAX_ACT) return LAS_ERR_UNSUPPORTED;
+  if (d->ncore + a == 0) return LAS_ERR_ARG;
+
+  las_ctx* x = (las_ctx*)calloc(1, sizeof(las_ctx));
+  if (!x) return LAS_ERR_INTERNAL;
+  x->n = d->nao;
+  x->X = d->naux;
+  x->nmo = d->nmo;
+  x->c = d->ncore;
+  x->a = a;
+  x->o = d->ncore + a;
+  x->op = (x->o + 15) / 16 * 16;
+  x->npair = (long)x->n * (x->n + 1) / 2;
+  x->prec = prec;
+  x->Bp = B_packed;
+  x->stream = (cudaStream_t)stream;
+  x->fi.nfrag = d->nfrag;
+  x->fi.ncore = d->ncore;
+  x->fi.nact = a;
+  long o1 = 0, o2 = 0;
+  x->fi.off[0] = 0;
+  for (int k = 0; k < d->nfrag; ++k) {
+    int m = d->nact[k];
+    x->fi.off[k + 1] = x->fi.off[k] + m;
+    x->fi.dm1_off[k] = o1;
+    x->fi.dm2_off[k] = o2;
+    o1 += 2L * m * m;
+    o2 += (long)m * m * m * m;
+  }
+  x->ndm1 = o1;
+  x->ndm2 = o2;
+  memset(&x->fi_c, 0, sizeof(x->fi_c));
+  x->fi_c.ncore = d->ncore;
+
+  // Workspace plan: the largest auxiliary chunk that fits the cap.
+  const size_t fixed = sizeof(double) * ((size_t)x->n * x->op * 4 + (size_t)x->op * x->op +
+                                         (size_t)x->nmo * x->op + 3 * (size_t)x->X + x->npair);
+  size_t cap = max_ws ? max_ws : (size_t)24 << 30;
+  int Lc = x->X;
+  while (Lc > 1 && fixed + chunk_bytes(x, Lc) + (size_t)64 * x->n * x->op * 8 > cap) Lc = (Lc + 1) / 2;
+  if (fixed + chunk_bytes(x, Lc) > cap) {
+    free(x);
+    return LAS_ERR_WORKSPACE;
+  }
+  x->Lc = Lc;
+  x->ws_cap = cap;
+  {
+    int tiles = ((x->n + 63) / 64) * ((x->op + 63) / 64);
+    int ks = (4 * 152 + tiles - 1) / tiles;
+    int kmax = std::max(1, (Lc * x->op) / 256);
+    x->ksplit = std::max(1, std::min(std::min(ks, 64), kmax));
+  }
+  las_status st = LAS_OK;
+#define ALLOC(ptr, count) \
+  if (st == LAS_OK) st = dalloc(x, (void**)&x->ptr, sizeof(*x->ptr) * (size_t)(count));
+  ALLOC(Cocc, (size_t)x->n * x->op);
+  ALLOC(Ht, (size_t)Lc * x->op * x->n);
+  ALLOC(T, (size_t)Lc * x->op * x->op);
+  ALLOC(W, (size_t)Lc * x->op * x->op);
+  ALLOC(part, (size_t)x->ksplit * x->n * x->op);
+  ALLOC(Out, (size_t)x->n * x->op);
+  ALLOC(hC, (size_t)x->n * x->op);
+  ALLOC(hmo, (size_t)x->op * x->op);
+  ALLOC(M, (size_t)x->nmo * x->op);
+  ALLOC(eps, x->X);
+  ALLOC(vc, x->X);
+  ALLOC(va, x->X);
+  ALLOC(Jp, x->npair);
+  ALLOC(status, 4);
+  ALLOC(dC, (size_t)x->n * x->nmo);
+  ALLOC(dh, (size_t)x->n * x->n);
+  ALLOC(ddm1, std::max(1L, x->ndm1));
+  ALLOC(ddm2, std::max(1L, x->ndm2));
+  ALLOC(dE, 1);
+  ALLOC(dG, (size_t)x->n * x->nmo);
+#undef ALLOC
+  if (st == LAS_OK) {
+    cudaError_t e = cudaMemsetAsync(x->status, 0, 4 * sizeof(int), x->stream);
+    if (e != cudaSuccess) {
+      las_record_cuda_error(e, "cudaMemsetAsync", __FILE__, __LINE__);
+      st = LAS_ERR_CUDA;
+    }
+  }
+  if (st == LAS_OK) {
+    st = per_aux_prepare(a);
+  }
+  if (st == LAS_OK && prec == LAS_SPLIT_BF16) {
+    st = split_create(&x->split, x->n, x->X, x->op, x->Lc, B_packed, x->stream, &x->bytes);
+  }
+  if (st == LAS_OK) {
+    cudaError_t e = cudaStreamSynchronize(x->stream);
+    if (e != cudaSuccess) {
+      las_record_cuda_error(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+      st = LAS_ERR_CUDA;
+    }
+  }
+  if (st != LAS_OK) {
+    free_all(x);
+    free(x);
+    return st;
+  }
+  *out = x;
+  return LAS_OK;
+}
+
+extern "C" las_status las_destroy(las_ctx* x) {
+  if (!x) return LAS_ERR_ARG;
+  cudaStreamSynchronize(x->stream);
+  free_all(x);
+  free(x);
+  return LAS_OK;
+}
+
+extern "C" las_status las_set_stream(las_ctx* x, void* stream) {
+  if (!x) return LAS_ERR_ARG;
+  x->stream = (cudaStream_t)stream;
+  return LAS_OK;
+}
+
+extern "C" size_t las_device_bytes(const las_ctx* x) { return x ? x->bytes : 0; }
+
+static las_status check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "kernel launch", __FILE__, __LINE__);
+    return LAS_ERR_CUDA;
+  }
+  return LAS_OK;
+}
+
+extern "C" las_status las_sync(las_ctx* x) {
+  if (!x) return LAS_ERR_ARG;
+  LAS_CUDA_TRY(cudaStreamSynchronize(x->stream));
+  int h[4] = {0, 0, 0, 0};
+  LAS_CUDA_TRY(cudaMemcpy(h, x->status, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h[0] != 0) return (las_status)h[0];
+  return LAS_OK;
+}
+
+extern "C" las_status las_set_timing(las_ctx* x, int enable) {
+  if (!x) return LAS_ERR_ARG;
+  if (enable && !x->ev[0])
+    for (int i = 0; i < 8; ++i) LAS_CUDA_TRY(cudaEventCreate(&x->ev[i]));
+  x->timing = enable;
+  return LAS_OK;
+}
+
+extern "C" int las_stage_times(las_ctx* x, float* ms, int cap) {
+  if (!x || !x->timing || x->nstage == 0) return 0;
+  if (cudaEventSynchronize(x->ev[x->nstage]) != cudaSuccess) return 0;
+  int k = 0;
+  for (; k < x->nstage && k < cap; ++k) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, x->ev[k], x->ev[k + 1]);
+    ms[k] = t;
+  }
+  return k;
+}
+
+static inline void stage_mark(las_ctx* x, int i) {
+  if (x->timing && i < 8) {
+    cudaEventRecord(x->ev[i], x->stream);
+    x->nstage = i;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Chain pieces
+// ------------------------------------------------------------------------------------------
+// S1 + S2 on auxiliary rows [l0, l0+nL): Ht[b][p][mu] = (b^L C_occ)(mu,p), T[b] = C_occ^T H
+static las_status half_and_full(las_ctx* x, int l0, int nL, int want_T) {
+  const int n = x->n, op = x->op;
+  if (x->prec == LAS_SPLIT_BF16) {
+    return split_half_full(x->split, l0, nL, x->Cocc, x->Ht, want_T ? x->T : nullptr,
+                           x->stream);
+  }
+  PackedSymA A{x->Bp, x->npair, l0};
+  StridedA Bm{x->Cocc, 0, op, 1};
+  StridedC Ch{x->Ht, (long)op * n, 1, n, 1.0, 0};
+  gemm_f64(n, op, n, nL, 1, A, Bm, Ch, x->stream);
+  if (want_T) {
+    StridedA Ah{x->Ht, (long)op * n, n, 1};
+    StridedC Ct{x->T, (long)op * op, op, 1, 1.0, 0};
+    gemm_f64(op, op, n, nL, 1, Ah, Bm, Ct, x->stream);
+  }
+  return check_launch();
+}
+
+// Out (+)= sum_{b < nL} Ht_b^T W_b   (n x op), split over K = nL*op, partials reduced in order
+static las_status project(las_ctx* x, int nL, int accumulate) {
+  const int n = x->n, op = x->op;
+  if (x->prec == LAS_SPLIT_BF16) {
+    return split_project(x->split, nL, x->Ht, x->W, x->Out, accumulate, x->stream);
+  }
+  int ks = std::max(1, std::min(x->ksplit, (nL * op) / 64));
+  StridedA A{x->Ht, 0, 1, n};
+  StridedA Bw{x->W, 0, op, 1};
+  StridedC Cp{x->part, (long)n * op, op, 1, 1.0, 0};
+  gemm_f64(n, op, nL * op, 1, ks, A, Bw, Cp, x->stream);
+  launch_reduce_partials(x->part, ks, (long)n * op, x->Out, accumulate, x->stream);
+  return check_launch();
+}
+
+static las_status evaluate(las_ctx* x, const double* C, const double* h, const double* dm1s,
+                           const double* dm2, double* E, double* G, double* gorb) {
+  if (!x || !C || !h || !E) return LAS_ERR_ARG;
+  if (x->a > 0 && (!dm1s || !dm2)) return LAS_ERR_ARG;
+  const int n = x->n, op = x->op, nmo = x->nmo;
+  const int with_grad = (G != nullptr) || (gorb != nullptr);
+  if (gorb && !G) G = x->dG;
+  las_status st;
+  stage_mark(x, 0);
+  launch_pack_cocc(C, n, nmo, x->o, op, x->Cocc, x->stream);
+  if (x->prec == LAS_SPLIT_BF16) {
+    st = split_prepare_C(x->split, x->Cocc, x->stream);
+    if (st != LAS_OK) return st;
+  }
+  for (int l0 = 0; l0 < x->X; l0 += x->Lc) {
+    const int nL = std::min(x->Lc, x->X - l0);
+    if ((st = half_and_full(x, l0, nL, 1)) != LAS_OK) return st;
+    if (l0 == 0) stage_mark(x, 1);
+    launch_per_aux(x->T, nL, op, dm1s, dm2, x->fi, x->W, x->eps + l0, x->vc + l0, x->va + l0,
+                   with_grad, x->status, x->stream);
+    if ((st = check_launch()) != LAS_OK) return st;
+    if (l0 == 0) stage_mark(x, 2);
+    if (with_grad && (st = project(x, nL, l0 > 0)) != LAS_OK) return st;
+  }
+  stage_mark(x, 3);
+  {  // one-electron pieces: hC = h C_occ, hmo = C_occ^T hC
+    StridedA Ah{h, 0, n, 1};
+    StridedA Bc{x->Cocc, 0, op, 1};
+    StridedC Ch{x->hC, 0, op, 1, 1.0, 0};
+    gemm_f64(n, op, n, 1, 1, Ah, Bc, Ch, x->stream);
+    StridedA Act{x->Cocc, 0, 1, op};
+    StridedA Bh{x->hC, 0, op, 1};
+    StridedC Cm{x->hmo, 0, op, 1, 1.0, 0};
+    gemm_f64(op, op, n, 1, 1, Act, Bh, Cm, x->stream);
+  }
+  launch_energy_final(x->eps, x->X, x->hmo, op, dm1s, x->fi, E, x->stream);
+  if (with_grad) {
+    launch_assemble_grad(x->Out, x->hC, dm1s, x->fi, n, nmo, op, G, x->stream);
+    if (gorb) {
+      StridedA Act{C, 0, 1, nmo};
+      StridedA Bg{G, 0, nmo, 1};
+      StridedC Cm{x->M, 0, op, 1, 1.0, 0};
+      gemm_f64(nmo, x->o, n, 1, 1, Act, Bg, Cm, x->stream);
+      launch_antisym(x->M, nmo, x->o, op, gorb, x->stream);
+    }
+  }
+  stage_mark(x, 4);
+  return check_launch();
+}
+
+extern "C" las_status las_energy(las_ctx* x, const double* C, const double* h,
+                                 const double* dm1s, const double* dm2, double* E) {
+  return evaluate(x, C, h, dm1s, dm2, E, nullptr, nullptr);
+}
+
+extern "C" las_status las_energy_grad(las_ctx* x, const double* C, const double* h,
+                                      const double* dm1s, const double* dm2, double* E,
+                                      double* dEdC, double* gorb) {
+  if (!dEdC && !gorb) return LAS_ERR_ARG;
+  return evaluate(x, C, h, dm1s, dm2, E, dEdC, gorb);
+}
+
+extern "C" las_status las_energy_grad_host(las_ctx* x, const double* C_host,
+                                           const double* h_host, const double* dm1s_host,
+                                           const double* dm2_host, double* E_host,
+                                           double* dEdC_host) {
+  if (!x || !C_host || !h_host || !E_host) return LAS_ERR_ARG;
+  if (x->a > 0 && (!dm1s_host || !dm2_host)) return LAS_ERR_ARG;
+  cudaStream_t s = x->stream;
+  const size_t nC = (size_t)x->n * x->nmo;
+  LAS_CUDA_TRY(cudaMemcpyAsync(x->dC, C_host, nC * 8, cudaMemcpyHostToDevice, s));
+  LAS_CUDA_TRY(cudaMemcpyAsync(x->dh, h_host, (size_t)x->n * x->n * 8, cudaMemcpyHostToDevice, s));
+  if (x->a > 0) {
+    LAS_CUDA_TRY(cudaMemcpyAsync(x->ddm1, dm1s_host, x->ndm1 * 8, cudaMemcpyHostToDevice, s));
+    LAS_CUDA_TRY(cudaMemcpyAsync(x->ddm2, dm2_host, x->ndm2 * 8, cudaMemcpyHostToDevice, s));
+  }
+  las_status st = evaluate(x, x->dC, x->dh, x->ddm1, x->ddm2, x->dE,
+                           dEdC_host ? x->dG : nullptr, nullptr);
+  if (st != LAS_OK) return st;
+  LAS_CUDA_TRY(cudaMemcpyAsync(E_host, x->dE, 8, cudaMemcpyDeviceToHost, s));
+  if (dEdC_host) LAS_CUDA_TRY(cudaMemcpyAsync(dEdC_host, x->dG, nC * 8, cudaMemcpyDeviceToHost, s));
+  return las_sync(x);
+}
+
+extern "C" las_status las_df_jk(las_ctx* x, const double* C, double* J, double* K) {
+  if (!x || !C) return LAS_ERR_ARG;
+  if (!J && !K) return LAS_OK;
+  const int n = x->n, op = x->op, c = x->c;
+  if (c == 0) {
+    if (J) LAS_CUDA_TRY(cudaMemsetAsync(J, 0, (size_t)n * n * 8, x->stream));
+    if (K) LAS_CUDA_TRY(cudaMemsetAsync(K, 0, (size_t)n * n * 8, x->stream));
+    return LAS_OK;
+  }
+  // core-only C_occ (columns >= c zeroed) so that H holds b^L C_core
+  launch_pack_cocc(C, n, x->nmo, c, op, x->Cocc, x->stream);
+  if (x->prec == LAS_SPLIT_BF16) {
+    las_status st = split_prepare_C(x->split, x->Cocc, x->stream);
+    if (st != LAS_OK) return st;
+  }
+  las_status st;
+  for (int l0 = 0; l0 < x->X; l0 += x->Lc) {
+    const int nL = std::min(x->Lc, x->X - l0);
+    if ((st = half_and_full(x, l0, nL, J != nullptr)) != LAS_OK) return st;
+    if (J) {  // vc_L = 2 sum_i T_L(i,i)
+      launch_per_aux(x->T, nL, op, nullptr, nullptr, x->fi_c, x->W, x->eps + l0,
+                     x->vc + l0, x->va + l0, 0, x->status, x->stream);
+    }
+    if (K) {  // K = 2 sum_{L,i} H_L(:,i) H_L(:,i)^T
+      StridedA A{x->Ht, 0, 1, n};
+      StridedA B{x->Ht, 0, n, 1};
+      int ks = std::max(1, std::min(x->ksplit, (nL * op) / 64));
+      // reuse `part` as [ks][n][n] only when it is large enough; otherwise accumulate directly
+      if ((size_t)ks * n * n <= (size_t)x->ksplit * n * op) {
+        StridedC Pk{x->part, (long)n * n, n, 1, 2.0, 0};
+        gemm_f64(n, n, nL * op, 1, ks, A, B, Pk, x->stream);
+        launch_reduce_partials(x->part, ks, (long)n * n, K, l0 > 0, x->stream);
+      } else {
+        StridedC Kd{K, 0, n, 1, 2.0, l0 > 0};
+        gemm_f64(n, n, nL * op, 1, 1, A, B, Kd, x->stream);
+      }
+    }
+    if ((st = check_launch()) != LAS_OK) return st;
+  }
+  if (J) {
+    launch_coulomb_packed(x->Bp, x->vc, x->X, x->npair, x->Jp, x->stream);
+    launch_unpack_sym(x->Jp, n, J, x->stream);
+  }
+  return check_launch();
+}
+
+extern "C" las_status las_df_transform(las_ctx* x, const double* C, int p0, int p1,
+                                       double* Lmu_u, double* Lpu) {
+  if (!x || !C) return LAS_ERR_ARG;
+  if (p0 < 0 || p1 < p0 || p1 > x->nmo) return LAS_ERR_ARG;
+  if (x->a == 0) return LAS_OK;
+  const int n = x->n, op = x->op, c = x->c, a = x->a, np = p1 - p0;
+  launch_pack_cocc(C, n, x->nmo, x->o, op, x->Cocc, x->stream);
+  if (x->prec == LAS_SPLIT_BF16) {
+    las_status st = split_prepare_C(x->split, x->Cocc, x->stream);
+    if (st != LAS_OK) return st;
+  }
+  las_status st;
+  for (int l0 = 0; l0 < x->X; l0 += x->Lc) {
+    const int nL = std::min(x->Lc, x->X - l0);
+    if ((st = half_and_full(x, l0, nL, 0)) != LAS_OK) return st;
+    if (Lmu_u) launch_copy_cols(x->Ht, nL, op, n, c, a, Lmu_u + (size_t)l0 * n * a, x->stream);
+    if (Lpu && np > 0) {
+      // Lpu[b][p][u] = sum_mu C[mu][p0+p] Ht[b][c+u][mu]
+      StridedA A{C + p0, 0, 1, x->nmo};
+      StridedA B{x->Ht + (size_t)c * n, (long)op * n, 1, n};
+      StridedC Co{Lpu + (size_t)l0 * np * a, (long)np * a, a, 1, 1.0, 0};
+      // batch over L: A is shared (sb = 0), B and C advance per L
+      gemm_f64(np, a, n, nL, 1, A, B, Co, x->stream);
+    }
+    if ((st = check_launch()) != LAS_OK) return st;
+  }
+  return LAS_OK;
+}

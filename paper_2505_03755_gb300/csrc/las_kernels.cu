@@ -1,0 +1,343 @@
+// Small FP64 kernels of the LAS energy/gradient chain: per-auxiliary-index contractions with the
+// block-product RDMs, energy reduction, gradient assembly and layout helpers.
+#include <algorithm>
+
+#include "las_common.cuh"
+
+namespace lasdf {
+
+// Deterministic block reduction of one double per thread (fixed tree order).
+template <int NT>
+__device__ double block_sum(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+#pragma unroll
+  for (int s = NT / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_pack_cocc(const double* __restrict__ C, int n, int nmo, int o, int op,
+                            double* __restrict__ Cocc) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long total = (long)n * op;
+  if (i >= total) return;
+  int mu = (int)(i / op), p = (int)(i % op);
+  Cocc[i] = (p < o) ? C[(long)mu * nmo + p] : 0.0;
+}
+
+__device__ __forceinline__ int frag_of(const FragInfo& fi, int u) {
+  int K = 0;
+  while (K + 1 < fi.nfrag && fi.off[K + 1] <= u) ++K;
+  return K;
+}
+
+// Per auxiliary index L (one CTA each), given T_L = C_occ^T b^L C_occ (op x op):
+//   vc = 2 sum_i T(i,i)                     (Coulomb vector of Dc, Eq. J_1 in the MO basis)
+//   va = sum_uv D_uv T(u,v)                 (Coulomb vector of the active density)
+//   Y(u,v) = sum_wx Gamma_uvwx T(w,x)       (block-product 2-RDM of Eq. las_wfn, applied
+//                                            fragment-block by fragment-block)
+//   eps_L  = vc^2/2 - sum_ij T(i,j)^2 + vc va - sum_{i,u} Z(i,u) T(i,u) + 1/2 sum_uv T(u,v) Y(u,v)
+//            with Z = T(core,act) D  (the L-th term of the two-electron energy)
+//   W_L(p,q): the matrix with  dE/dC(two-electron part) = sum_L H_L W_L, H_L = b^L C_occ.
+__global__ void __launch_bounds__(256)
+k_per_aux(const double* __restrict__ T, int op, const double* __restrict__ dm1s,
+          const double* __restrict__ dm2, FragInfo fi, double* __restrict__ W,
+          double* __restrict__ eps, double* __restrict__ vcv, double* __restrict__ vav,
+          int with_grad, int* status) {
+  extern __shared__ double sm[];
+  const int a = fi.nact, c = fi.ncore, o = c + a;
+  double* Taa = sm;             // a*a
+  double* Ds = Taa + a * a;     // a*a (block diagonal D)
+  double* Y = Ds + a * a;       // a*a
+  double* red = Y + a * a;      // 256
+  double* cK = red + 256;       // nfrag
+  const long Lb = blockIdx.x;
+  const double* TL = T + Lb * (long)op * op;
+  const int tid = threadIdx.x;
+
+  for (int i = tid; i < a * a; i += 256) {
+    int u = i / a, v = i % a;
+    Taa[i] = TL[(long)(c + u) * op + c + v];
+    int K = frag_of(fi, u);
+    double d = 0.0;
+    if (v >= fi.off[K] && v < fi.off[K + 1]) {
+      int m = fi.off[K + 1] - fi.off[K];
+      int uu = u - fi.off[K], vv = v - fi.off[K];
+      const double* g = dm1s + fi.dm1_off[K];
+      d = g[uu * m + vv] + g[m * m + uu * m + vv];
+    }
+    Ds[i] = d;
+  }
+  __syncthreads();
+
+  double pvc = 0.0, pcore = 0.0;
+  for (int i = tid; i < c; i += 256) pvc += TL[(long)i * op + i];
+  for (long i = tid; i < (long)c * c; i += 256) {
+    double x = TL[(i / c) * op + (i % c)];
+    pcore += x * x;
+  }
+  double pva = 0.0;
+  for (int i = tid; i < a * a; i += 256) pva += Ds[i] * Taa[i];
+  const double vc = 2.0 * block_sum<256>(pvc, red);
+  const double fro = block_sum<256>(pcore, red);
+  const double va = block_sum<256>(pva, red);
+  if (tid < fi.nfrag) {
+    int K = tid, o0 = fi.off[K], m = fi.off[K + 1] - o0;
+    double s = 0.0;
+    for (int u = 0; u < m; ++u)
+      for (int v = 0; v < m; ++v) s += Ds[(o0 + u) * a + o0 + v] * Taa[(o0 + u) * a + o0 + v];
+    cK[K] = s;
+  }
+  __syncthreads();
+
+  // Y = Gamma . T over the active block, fragment structure of Eq. las_wfn.
+  for (int i = tid; i < a * a; i += 256) {
+    const int u = i / a, v = i % a;
+    const int K = frag_of(fi, u), Kp = frag_of(fi, v);
+    const int oK = fi.off[K], mK = fi.off[K + 1] - oK;
+    double y = 0.0;
+    if (K == Kp) {
+      const double* g2 = dm2 + fi.dm2_off[K];
+      const int uu = u - oK, vv = v - oK;
+      const double* gr = g2 + ((long)uu * mK + vv) * mK * mK;
+      for (int w = 0; w < mK; ++w)
+        for (int x = 0; x < mK; ++x) y += gr[w * mK + x] * Taa[(oK + w) * a + oK + x];
+      y += Ds[i] * (va - cK[K]);
+    } else {
+      // -sum_sigma sum_{x in K, w in K'} gK_s[u,x] T(x,w) gK'_s[w,v]
+      const int oP = fi.off[Kp], mP = fi.off[Kp + 1] - oP;
+      const double* gK = dm1s + fi.dm1_off[K];
+      const double* gP = dm1s + fi.dm1_off[Kp];
+      const int uu = u - oK, vv = v - oP;
+      for (int s = 0; s < 2; ++s) {
+        const double* gKs = gK + s * mK * mK;
+        const double* gPs = gP + s * mP * mP;
+        for (int x = 0; x < mK; ++x) {
+          double gux = gKs[uu * mK + x];
+          if (gux == 0.0) continue;
+          double t = 0.0;
+          for (int w = 0; w < mP; ++w) t += Taa[(oK + x) * a + oP + w] * gPs[w * mP + vv];
+          y -= gux * t;
+        }
+      }
+    }
+    Y[i] = y;
+  }
+  __syncthreads();
+
+  // Z(i,u) = sum_v T(i, c+v) D(v,u) over core i and active u; its contraction with T(i,u).
+  double pz = 0.0;
+  double* WL = W + Lb * (long)op * op;
+  for (long idx = tid; idx < (long)c * a; idx += 256) {
+    const int i = (int)(idx / a), u = (int)(idx % a);
+    const int K = frag_of(fi, u), oK = fi.off[K], mK = fi.off[K + 1] - oK;
+    const double* Ti = TL + (long)i * op + c;
+    double z = 0.0;
+    for (int v = oK; v < oK + mK; ++v) z += Ti[v] * Ds[v * a + u];
+    pz += z * Ti[u];
+    if (with_grad) {
+      WL[(long)i * op + c + u] = -2.0 * z;
+      WL[(long)(c + u) * op + i] = -2.0 * z;
+    }
+  }
+  double pe = 0.0;
+  for (int i = tid; i < a * a; i += 256) pe += Taa[i] * Y[i];
+  const double zt = block_sum<256>(pz, red);
+  const double ty = block_sum<256>(pe, red);
+  if (tid == 0) {
+    eps[Lb] = 0.5 * vc * vc - fro + vc * va - zt + 0.5 * ty;
+    vcv[Lb] = vc;
+    vav[Lb] = va;
+  }
+  if (!with_grad) return;
+  // core-core block, active-active block and zero padding
+  for (long idx = tid; idx < (long)op * op; idx += 256) {
+    const int p = (int)(idx / op), q = (int)(idx % op);
+    double w;
+    if (p < c && q < c) {
+      w = -4.0 * TL[idx] + (p == q ? 4.0 * (vc + va) : 0.0);
+    } else if (p >= c && p < o && q >= c && q < o) {
+      const int wv = p - c, u = q - c;
+      w = 2.0 * vc * Ds[wv * a + u] + 2.0 * Y[u * a + wv];
+    } else if (p >= o || q >= o) {
+      w = 0.0;
+    } else {
+      continue;  // core/active blocks written above
+    }
+    WL[idx] = w;
+  }
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ part, int nsplit, long count,
+                                  double* __restrict__ out, int accumulate) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double s = accumulate ? out[i] : 0.0;
+  for (int k = 0; k < nsplit; ++k) s += part[(long)k * count + i];
+  out[i] = s;
+}
+
+// dE/dC = [4 h C_core | 2 h C_act D | 0] + Out   (Out = sum_L H_L W_L, n x op)
+__global__ void k_assemble_grad(const double* __restrict__ Out, const double* __restrict__ hC,
+                                const double* __restrict__ dm1s, FragInfo fi, int n, int nmo,
+                                int op, double* __restrict__ G) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= (long)n * nmo) return;
+  const int mu = (int)(i / nmo), q = (int)(i % nmo);
+  const int c = fi.ncore, o = c + fi.nact;
+  double g = 0.0;
+  if (q < c) {
+    g = 4.0 * hC[(long)mu * op + q] + Out[(long)mu * op + q];
+  } else if (q < o) {
+    const int u = q - c;
+    const int K = frag_of(fi, u), oK = fi.off[K], m = fi.off[K + 1] - oK;
+    const double* gK = dm1s + fi.dm1_off[K];
+    double s = 0.0;
+    for (int v = 0; v < m; ++v) {
+      double d = gK[v * m + (u - oK)] + gK[m * m + v * m + (u - oK)];
+      s += hC[(long)mu * op + c + oK + v] * d;
+    }
+    g = 2.0 * s + Out[(long)mu * op + q];
+  }
+  G[i] = g;
+}
+
+// E = 2 sum_i hmo(i,i) + sum_uv hmo(c+u,c+v) D_uv + sum_L eps_L  (one CTA, fixed order,
+// compensated summation).
+__global__ void __launch_bounds__(256)
+k_energy_final(const double* __restrict__ eps, int X, const double* __restrict__ hmo, int op,
+               const double* __restrict__ dm1s, FragInfo fi, double* __restrict__ E) {
+  __shared__ double red[256];
+  double s = 0.0, comp = 0.0;
+  auto add = [&](double x) {  // Neumaier
+    double t = s + x;
+    if (fabs(s) >= fabs(x)) comp += (s - t) + x; else comp += (x - t) + s;
+    s = t;
+  };
+  for (int L = threadIdx.x; L < X; L += 256) add(eps[L]);
+  const int c = fi.ncore;
+  for (int i = threadIdx.x; i < c; i += 256) add(2.0 * hmo[(long)i * op + i]);
+  for (int K = 0; K < fi.nfrag; ++K) {
+    const int oK = fi.off[K], m = fi.off[K + 1] - oK;
+    const double* g = dm1s + fi.dm1_off[K];
+    for (int i = threadIdx.x; i < m * m; i += 256) {
+      const int u = i / m, v = i % m;
+      add(hmo[(long)(c + oK + u) * op + c + oK + v] * (g[i] + g[m * m + i]));
+    }
+  }
+  double tot = block_sum<256>(s + comp, red);
+  if (threadIdx.x == 0) *E = tot;
+}
+
+// g[p][q] = M'[p][q] - M'[q][p],  M'[p][q] = M[p][q] for q < o else 0  (M is nmo x op)
+__global__ void k_antisym(const double* __restrict__ M, int nmo, int o, int op,
+                          double* __restrict__ g) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= (long)nmo * nmo) return;
+  const int p = (int)(i / nmo), q = (int)(i % nmo);
+  double x = (q < o) ? M[(long)p * op + q] : 0.0;
+  double y = (p < o) ? M[(long)q * op + p] : 0.0;
+  g[i] = x - y;
+}
+
+// Jp[pair] = sum_L vc[L] Bp[L][pair]  (Eq. J_2 on the packed triangle; coalesced along pairs)
+__global__ void k_coulomb_packed(const double* __restrict__ Bp, const double* __restrict__ vc,
+                                 int X, long npair, double* __restrict__ Jp) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= npair) return;
+  double s = 0.0;
+  for (int L = 0; L < X; ++L) s += vc[L] * Bp[(long)L * npair + i];
+  Jp[i] = s;
+}
+
+__global__ void k_unpack_sym(const double* __restrict__ Jp, int n, double* __restrict__ J) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= (long)n * n) return;
+  long mu = i / n, nu = i % n;
+  long hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
+  J[i] = Jp[hi * (hi + 1) / 2 + lo];
+}
+
+// Lmu[L][mu][u] = Ht[L][c0+u][mu]
+__global__ void k_copy_cols(const double* __restrict__ Ht, int X, int op, int n, int c0, int a,
+                            double* __restrict__ Lmu) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long total = (long)X * n * a;
+  if (i >= total) return;
+  const int u = (int)(i % a);
+  const long r = i / a;
+  const int mu = (int)(r % n);
+  const long L = r / n;
+  Lmu[i] = Ht[(L * op + c0 + u) * n + mu];
+}
+
+}  // namespace lasdf
+
+using namespace lasdf;
+
+static inline unsigned nblk(long count, int nt) { return (unsigned)((count + nt - 1) / nt); }
+
+void launch_pack_cocc(const double* C, int n, int nmo, int o, int op, double* Cocc,
+                      cudaStream_t s) {
+  k_pack_cocc<<<nblk((long)n * op, 256), 256, 0, s>>>(C, n, nmo, o, op, Cocc);
+}
+
+las_status per_aux_prepare(int nact) {
+  // always the largest supported size, so that contexts with different active spaces coexist
+  (void)nact;
+  size_t smem = (3 * (size_t)LAS_MAX_ACT * LAS_MAX_ACT + 256 + LAS_MAX_FRAG) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_per_aux, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)std::max<size_t>(smem, 48 * 1024));
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "cudaFuncSetAttribute(k_per_aux)", __FILE__, __LINE__);
+    return LAS_ERR_CUDA;
+  }
+  return LAS_OK;
+}
+
+void launch_per_aux(const double* T, int nL, int op, const double* dm1s, const double* dm2,
+                    const FragInfo& fi, double* W, double* eps, double* vc, double* va,
+                    int with_grad, int* status, cudaStream_t s) {
+  if (nL <= 0) return;
+  size_t smem = (3 * (size_t)fi.nact * fi.nact + 256 + LAS_MAX_FRAG) * sizeof(double);
+  k_per_aux<<<nL, 256, smem, s>>>(T, op, dm1s, dm2, fi, W, eps, vc, va, with_grad, status);
+}
+
+void launch_reduce_partials(const double* part, int nsplit, long count, double* out,
+                            int accumulate, cudaStream_t s) {
+  k_reduce_partials<<<nblk(count, 256), 256, 0, s>>>(part, nsplit, count, out, accumulate);
+}
+
+void launch_assemble_grad(const double* Out, const double* hC, const double* dm1s,
+                          const FragInfo& fi, int n, int nmo, int op, double* G,
+                          cudaStream_t s) {
+  k_assemble_grad<<<nblk((long)n * nmo, 256), 256, 0, s>>>(Out, hC, dm1s, fi, n, nmo, op, G);
+}
+
+void launch_energy_final(const double* eps, int X, const double* hmo, int op,
+                         const double* dm1s, const FragInfo& fi, double* E, cudaStream_t s) {
+  k_energy_final<<<1, 256, 0, s>>>(eps, X, hmo, op, dm1s, fi, E);
+}
+
+void launch_antisym(const double* M, int nmo, int o, int op, double* g, cudaStream_t s) {
+  k_antisym<<<nblk((long)nmo * nmo, 256), 256, 0, s>>>(M, nmo, o, op, g);
+}
+
+void launch_coulomb_packed(const double* Bp, const double* vc, int X, long npair, double* Jp,
+                           cudaStream_t s) {
+  k_coulomb_packed<<<nblk(npair, 256), 256, 0, s>>>(Bp, vc, X, npair, Jp);
+}
+
+void launch_unpack_sym(const double* Jp, int n, double* J, cudaStream_t s) {
+  k_unpack_sym<<<nblk((long)n * n, 256), 256, 0, s>>>(Jp, n, J);
+}
+
+void launch_copy_cols(const double* Ht, int X, int op, int n, int c0, int a, double* Lmu,
+                      cudaStream_t s) {
+  k_copy_cols<<<nblk((long)X * n * a, 256), 256, 0, s>>>(Ht, X, op, n, c0, a, Lmu);
+}

@@ -1,0 +1,234 @@
+"""Thin Python binding of liblasdf (argument marshalling only; every step runs in CUDA).
+
+PyTorch is used for device memory and streams.  All tensors passed in must be contiguous
+float64 CUDA tensors.  Nothing here computes any part of the LAS energy or gradient: a missing
+or unloadable shared library raises immediately (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblasdf.so")
+
+LAS_FP64 = 0
+LAS_SPLIT_BF16 = 1
+PRECISIONS = {"fp64": LAS_FP64, "split": LAS_SPLIT_BF16, "split_bf16": LAS_SPLIT_BF16}
+
+EXPORTS = ["las_create", "las_destroy", "las_set_stream", "las_sync", "las_device_bytes",
+           "las_df_transform", "las_df_jk", "las_energy", "las_energy_grad",
+           "las_energy_grad_host", "las_set_timing", "las_stage_times", "las_status_str"]
+
+
+class LasError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: status {code} ({msg})")
+        self.code = code
+
+
+class _Dims(ctypes.Structure):
+    _fields_ = [("nao", ctypes.c_int), ("naux", ctypes.c_int), ("nmo", ctypes.c_int),
+                ("ncore", ctypes.c_int), ("nfrag", ctypes.c_int),
+                ("nact", ctypes.POINTER(ctypes.c_int))]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the in-tree liblasdf.so (built by paper_2505_03755_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"liblasdf.so not found at {path}: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    lib.las_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Dims), vp, i, sz, vp]
+    lib.las_destroy.argtypes = [vp]
+    lib.las_set_stream.argtypes = [vp, vp]
+    lib.las_sync.argtypes = [vp]
+    lib.las_device_bytes.argtypes = [vp]
+    lib.las_device_bytes.restype = sz
+    lib.las_df_transform.argtypes = [vp, vp, i, i, vp, vp]
+    lib.las_df_jk.argtypes = [vp, vp, vp, vp]
+    lib.las_energy.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.las_energy_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.las_energy_grad_host.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.las_set_timing.argtypes = [vp, i]
+    lib.las_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
+    lib.las_stage_times.restype = i
+    lib.las_status_str.argtypes = [i]
+    lib.las_status_str.restype = ctypes.c_char_p
+    for name in ["las_create", "las_destroy", "las_set_stream", "las_sync", "las_df_transform",
+                 "las_df_jk", "las_energy", "las_energy_grad", "las_energy_grad_host",
+                 "las_set_timing"]:
+        getattr(lib, name).restype = i
+    _lib = lib
+    return lib
+
+
+def _check(code: int, where: str) -> None:
+    if code != 0:
+        msg = _lib.las_status_str(code).decode() if _lib is not None else "?"
+        raise LasError(code, where, msg)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("tensors must be contiguous float64 CUDA tensors")
+    return t.data_ptr()
+
+
+def _hptr(a) -> int | None:
+    if a is None:
+        return None
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise TypeError("host buffers must be C-contiguous float64 numpy arrays")
+    return a.ctypes.data
+
+
+class LasDF:
+    """One LAS problem (packed Cholesky vectors resident on the GPU) and its workspace."""
+
+    def __init__(self, B_packed, nao: int, naux: int, nmo: int, ncore: int, nact: list[int],
+                 precision: str = "fp64", max_workspace_bytes: int = 0, stream=None):
+        import torch
+        lib = load_library()
+        self._lib = lib
+        self.nao, self.naux, self.nmo, self.ncore = nao, naux, nmo, ncore
+        self.nact = list(nact)
+        self.precision = precision
+        self._B = B_packed  # keep the referenced device buffer alive
+        if B_packed.numel() != naux * nao * (nao + 1) // 2:
+            raise ValueError("B_packed must hold naux * nao(nao+1)/2 values")
+        arr = (ctypes.c_int * max(1, len(self.nact)))(*self.nact)
+        self._nact_arr = arr
+        dims = _Dims(nao, naux, nmo, ncore, len(self.nact), arr)
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(lib.las_create(ctypes.byref(h), ctypes.byref(dims), _ptr(B_packed),
+                              PRECISIONS[precision], max_workspace_bytes,
+                              self._stream.cuda_stream), "las_create")
+        self._h = h
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.las_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def device_bytes(self) -> int:
+        return int(self._lib.las_device_bytes(self._h))
+
+    def sync(self) -> None:
+        _check(self._lib.las_sync(self._h), "las_sync")
+
+    def set_timing(self, on: bool) -> None:
+        _check(self._lib.las_set_timing(self._h, int(on)), "las_set_timing")
+
+    def stage_times(self) -> list[float]:
+        buf = (ctypes.c_float * 8)()
+        k = self._lib.las_stage_times(self._h, buf, 8)
+        return [buf[i] for i in range(k)]
+
+    def energy(self, C, h, dm1s, dm2, E=None):
+        import torch
+        if E is None:
+            E = torch.empty((), dtype=torch.float64, device=C.device)
+        _check(self._lib.las_energy(self._h, _ptr(C), _ptr(h), _ptr(dm1s), _ptr(dm2), _ptr(E)),
+               "las_energy")
+        return E
+
+    def energy_grad(self, C, h, dm1s, dm2, want_gorb: bool = False, E=None, G=None, g=None):
+        import torch
+        dev = C.device
+        if E is None:
+            E = torch.empty((), dtype=torch.float64, device=dev)
+        if G is None:
+            G = torch.empty((self.nao, self.nmo), dtype=torch.float64, device=dev)
+        if want_gorb and g is None:
+            g = torch.empty((self.nmo, self.nmo), dtype=torch.float64, device=dev)
+        _check(self._lib.las_energy_grad(self._h, _ptr(C), _ptr(h), _ptr(dm1s), _ptr(dm2),
+                                         _ptr(E), _ptr(G), _ptr(g)), "las_energy_grad")
+        return (E, G, g) if want_gorb else (E, G)
+
+    def energy_grad_host(self, C, h, dm1s, dm2, with_grad: bool = True):
+        E = np.zeros(1)
+        G = np.empty((self.nao, self.nmo)) if with_grad else None
+        _check(self._lib.las_energy_grad_host(self._h, _hptr(C), _hptr(h), _hptr(dm1s),
+                                              _hptr(dm2), _hptr(E), _hptr(G)),
+               "las_energy_grad_host")
+        return float(E[0]), G
+
+    def df_jk(self, C, J=None, K=None):
+        import torch
+        n = self.nao
+        J = torch.empty((n, n), dtype=torch.float64, device=C.device) if J is None else J
+        K = torch.empty((n, n), dtype=torch.float64, device=C.device) if K is None else K
+        _check(self._lib.las_df_jk(self._h, _ptr(C), _ptr(J), _ptr(K)), "las_df_jk")
+        return J, K
+
+    def df_transform(self, C, p0: int, p1: int, want_lmu: bool = True, want_lpu: bool = True):
+        import torch
+        a = sum(self.nact)
+        dev = C.device
+        lmu = torch.empty((self.naux, self.nao, a), dtype=torch.float64, device=dev) \
+            if want_lmu else None
+        lpu = torch.empty((self.naux, p1 - p0, a), dtype=torch.float64, device=dev) \
+            if want_lpu else None
+        _check(self._lib.las_df_transform(self._h, _ptr(C), p0, p1, _ptr(lmu), _ptr(lpu)),
+               "las_df_transform")
+        return lmu, lpu
+
+
+def _energy_function():
+    import torch
+
+    class LasEnergy(torch.autograd.Function):
+        """E(C) with the hand-written adjoint: forward runs las_energy_grad (when C needs a
+        gradient) and keeps dE/dC; backward scales it by the incoming gradient."""
+
+        @staticmethod
+        def forward(ctx, C, las: LasDF, h, dm1s, dm2):
+            if ctx.needs_input_grad[0]:
+                E, G = las.energy_grad(C.detach().contiguous(), h, dm1s, dm2)
+                ctx.save_for_backward(G)
+            else:
+                E = las.energy(C.detach().contiguous(), h, dm1s, dm2)
+            return E
+
+        @staticmethod
+        def backward(ctx, gE):
+            (G,) = ctx.saved_tensors
+            return gE * G, None, None, None, None
+
+    return LasEnergy
+
+
+_LasEnergy = None
+
+
+def las_energy(C, las: LasDF, h, dm1s, dm2):
+    """Differentiable LAS energy E(C) (torch.autograd); dE/dC comes from the CUDA adjoint."""
+    global _LasEnergy
+    if _LasEnergy is None:
+        _LasEnergy = _energy_function()
+    return _LasEnergy.apply(C, las, h, dm1s, dm2)
