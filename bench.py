@@ -1,0 +1,361 @@
+"""Benchmark: LAS energy+gradient evaluations per second at Nao=1200 (Naux=4800, Ncore=150,
+(22e,40o) over 5 fragments), native FP64 versus split precision, with roofline fractions.
+
+One step = one full energy + dE/dC evaluation (every stage of the chain) over the resident,
+synthetic, seeded Cholesky vectors (27.7 GB packed FP64, far larger than L2, so no L2 flush is
+needed between steps).  Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision split|fp64|both]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample of the workload
+
+Under torchrun (N > 1) every rank evaluates its own system (independent problems, no data-path
+collective: weak scaling); the timed region is bracketed by barriers and the max over ranks is
+used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(config="nao1200_naux4800_core150_act22e40o_5frag", nao=1200, naux=4800,
+                ncore=150, frags=[(6, 8)] + [(4, 8)] * 4)
+METRIC = "LAS energy+gradient evals/s at Nao=1200 (FP64 vs split-prec), % of roofline"
+FP64_NOMINAL_TFLOPS = 1.25      # recipe nominal FP64 (DFMA/DMMA) for GB300
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def measured_peaks() -> dict:
+    try:
+        return json.load(open(PEAKS_FILE))
+    except Exception:
+        return {}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_work(nao, naux, ncore, nact):
+    """FP64-equivalent flops of one energy+gradient evaluation and of the dominant transform."""
+    n, X, c, a = nao, naux, ncore, nact
+    o = c + a
+    s1 = 2.0 * X * n * n * o                       # half transform (the dominant kernel)
+    s2 = 2.0 * X * n * o * o                       # occupied full transform
+    s6 = 2.0 * X * n * o * o                       # projections (J_2, K_2, active gradient)
+    return dict(s1=s1, s2=s2, s6=s6, total=s1 + s2 + s6)
+
+
+def make_inputs(rank: int):
+    from las_inputs import BASE_SEED, make_system
+    w = WORKLOAD
+    t0 = time.time()
+    s = make_system(w["nao"], w["naux"], w["ncore"], w["frags"], seed=BASE_SEED + 2 + 1000 * rank)
+    return s, time.time() - t0
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2505_03755_gb300 import LasDF, kernel_launches
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    s, tgen = make_inputs(rank)
+    Bd = torch.from_numpy(s.Bp).to(dev)
+    s.Bp = None
+    C = torch.from_numpy(s.C).to(dev)
+    h = torch.from_numpy(s.h).to(dev)
+    d1 = torch.from_numpy(s.dm1s_flat()).to(dev)
+    d2 = torch.from_numpy(s.dm2_flat()).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    work = algorithmic_work(s.nao, s.naux, s.ncore, s.nactive)
+    peaks = measured_peaks()
+
+    precs = ["split", "fp64"] if args.precision == "both" else [args.precision]
+    results = {}
+    for prec in precs:
+        steps = args.steps if prec == precs[0] else max(1, min(args.steps, args.fp64_steps))
+        warm = args.warmup if prec == precs[0] else max(1, min(args.warmup, args.fp64_warmup))
+        try:
+            las = LasDF(Bd, s.nao, s.naux, s.nmo, s.ncore, s.nact, precision=prec, stream=stream)
+        except Exception as e:  # a mode this build does not provide
+            results[prec] = {"error": str(e)}
+            continue
+        E = torch.empty((), dtype=torch.float64, device=dev)
+        G = torch.empty((s.nao, s.nmo), dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(warm):
+                las.energy_grad(C, h, d1, d2, E=E, G=G)
+            las.sync()
+            las.set_timing(True)
+            if ws > 1:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            clocks = ClockSampler(local)
+            clocks.start()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            launches0 = kernel_launches()
+            stage_acc = None
+            ev0.record(stream)
+            for _ in range(steps):
+                las.energy_grad(C, h, d1, d2, E=E, G=G)
+                st = las.stage_times()       # waits on this step's last event
+                stage_acc = st if stage_acc is None else [x + y for x, y in zip(stage_acc, st)]
+            ev1.record(stream)
+            ev1.synchronize()
+            launches = kernel_launches() - launches0
+            torch.cuda.synchronize(dev)
+            if ws > 1:
+                dist.barrier()
+            ck = clocks.stop()
+            las.set_timing(False)
+        ms = ev0.elapsed_time(ev1)
+        if ws > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        stage_ms = [x / steps for x in (stage_acc or [])]
+        E_val = float(E.item())
+
+        # end to end through the host-buffer C-ABI call (H2D of the step's inputs, D2H of E and
+        # dE/dC inside the timed region), pinned host buffers
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        Ch, hh, d1h, d2h = pin(s.C), pin(s.h), pin(s.dm1s_flat()), pin(s.dm2_flat())
+        Gh = torch.empty((s.nao, s.nmo), dtype=torch.float64).pin_memory().numpy()
+        with torch.cuda.stream(stream):
+            las.energy_grad_host(Ch, hh, d1h, d2h)
+            if ws > 1:
+                dist.barrier()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                e2e_E, _ = las.energy_grad_host(Ch, hh, d1h, d2h)
+            t_e2e = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        bi = Ch.nbytes + hh.nbytes + d1h.nbytes + d2h.nbytes
+        bo = 8 + Gh.nbytes
+        las.close()
+        results[prec] = dict(ms_per_step=ms / steps, steps=steps, warmup=warm,
+                             evals_per_s=ws * steps / (ms / 1e3), stage_ms=stage_ms,
+                             E=E_val, e2e_evals_per_s=ws * steps / t_e2e, e2e_E=e2e_E,
+                             h2d=bi, d2h=bo, clocks=ck, launches=launches)
+    del Bd
+    torch.cuda.empty_cache()
+    return s, work, peaks, results, tgen
+
+
+def roofline_for(prec, r, work, peaks, s):
+    if "stage_ms" not in r or not r["stage_ms"]:
+        return None
+    t_s1 = r["stage_ms"][0] / 1e3
+    if prec == "fp64":
+        achieved = work["s1"] / t_s1 / 1e12
+        return {"bound": "tensor", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "kernel": "k_gemm_f64 (half transform, DMMA)",
+                "peak_source": "nominal FP64 of the recipe (no measured FP64 peak in "
+                               "MEASURED_PEAKS.json)"}
+    return None
+
+
+def cpu_baseline(sample_rows: int):
+    """The oracle as it stands, on auxiliary rows [0, sample_rows) of the same workload,
+    scaled to a full evaluation."""
+    from las_inputs import BASE_SEED, make_system
+    from oracle import las_oracle as O
+    w = WORKLOAD
+    s = make_system(w["nao"], w["naux"], w["ncore"], w["frags"], seed=BASE_SEED + 2,
+                    with_B=False)
+    # the first sample_rows rows of the full-size B (same seed and counter layout)
+    Bs = _first_rows_B(BASE_SEED + 2, w["nao"], w["naux"], sample_rows)
+    t0 = time.perf_counter()
+    O.energy_grad(Bs, s.nao, s.h, s.C, s.ncore, s.dm1s, s.dm2, with_grad=True)
+    dt = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max(int(i.get("num_threads", 1)) for i in threadpool_info()) or os.cpu_count()
+    except Exception:
+        cores = os.cpu_count()
+    per_eval = dt * w["naux"] / sample_rows
+    return dict(value=1.0 / per_eval, unit="evals/s", cores=cores, kind="oracle",
+                sample=f"auxiliary rows [0,{sample_rows}) of {w['naux']} (one energy+gradient "
+                       f"over that slice, {dt:.1f} s), scaled by {w['naux']}/{sample_rows}",
+                seconds=dt)
+
+
+def _first_rows_B(seed, n, naux, rows):
+    from las_inputs.gen import normals, npair
+    import numpy as _np
+    P = npair(n)
+    mu, nu = _np.tril_indices(n)
+    decay = _np.exp(-_np.abs(mu - nu).astype(_np.float64) / 8.0)
+    out = _np.empty((rows, P))
+    for L in range(rows):
+        out[L] = normals(seed, 0, L * P, P) * decay * _np.exp(-L / naux)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="both", choices=["both", "split", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-warmup", type=int, default=3)
+    ap.add_argument("--cpu-rows", type=int, default=240)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.perf_counter()
+        vals = []
+        for _ in range(args.warmup):
+            cpu_baseline(max(1, args.cpu_rows // 8))
+        for _ in range(args.steps):
+            vals.append(cpu_baseline(args.cpu_rows))
+        v = statistics.median([x["value"] for x in vals])
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+                "config": {"workload": WORKLOAD["config"], "nao": 1200, "naux": 4800,
+                           "ncore": 150, "active": "(22e,40o) as 5x8 orbitals"},
+                "cpu_baseline": {"value": v, "unit": "evals/s", "cores": vals[0]["cores"],
+                                 "kind": "oracle", "sample": vals[0]["sample"]},
+                "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0},
+                "wall_s": time.perf_counter() - t0}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    s, work, peaks, res, tgen = run_ours(args, ws, rank, local)
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    primary = "split" if ("split" in res and "error" not in res["split"]) else "fp64"
+    r = res[primary]
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(args.cpu_rows)
+    modes = {}
+    for k, v in res.items():
+        if "error" in v:
+            modes[k] = {"error": v["error"]}
+            continue
+        modes[k] = {"evals_per_s": v["evals_per_s"], "ms_per_step": v["ms_per_step"],
+                    "steps": v["steps"], "E": v["E"],
+                    "fp64_equiv_tflops": work["total"] / (v["ms_per_step"] / 1e3) / 1e12,
+                    "stage_ms": v["stage_ms"], "roofline": roofline_for(k, v, work, peaks, s),
+                    "e2e_evals_per_s": v["e2e_evals_per_s"]}
+    line = {"metric": METRIC, "value": r["evals_per_s"], "unit": "evals/s", "n_gpus": ws,
+            "steps": r["steps"], "warmup": r["warmup"], "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if primary == "fp64" else "bf16-digits->f64",
+            "data": "synthetic (seeded counter-based generator; shapes of the paper's systems)",
+            "config": {"workload": WORKLOAD["config"], "nao": 1200, "naux": 4800, "ncore": 150,
+                       "active": "(22e,40o) as (6e,8o)+4x(4e,8o)", "precision": primary,
+                       "l2": "no flush: resident inputs (27.7 GB B) far exceed L2",
+                       "parallelism": f"{ws} independent system(s), one per GPU"},
+            "roofline": roofline_for(primary, r, work, peaks, s),
+            "cpu_baseline": cpu,
+            "e2e": {"value": r["e2e_evals_per_s"], "unit": "evals/s",
+                    "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+            "gpu_launches": r["launches"], "clocks": r["clocks"], "modes": modes,
+            "input_generation_s": tgen}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

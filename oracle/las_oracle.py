@@ -87,10 +87,11 @@ def df_jk(Bp: np.ndarray, n: int, dms: list[np.ndarray], l0: int = 0, l1: int | 
     K = [np.zeros((n, n)) for _ in dms]
     for _, _, b in p_blocks(Bp, n, l0, l1):
         for t, D in enumerate(dms):
-            vP = np.einsum("Pij,ij->P", b, D)           # Eq. J_1
-            J[t] += np.einsum("P,Pij->ij", vP, b)       # Eq. J_2
-            vPik = b @ D                                 # Eq. K_1
-            K[t] += np.einsum("Pik,Pjk->ij", vPik, b)   # Eq. K_2
+            nb = b.shape[0]
+            vP = b.reshape(nb, n * n) @ D.reshape(n * n)                 # Eq. J_1
+            J[t] += (vP @ b.reshape(nb, n * n)).reshape(n, n)           # Eq. J_2
+            vPik = b @ D                                                 # Eq. K_1
+            K[t] += np.einsum("Pik,Pjk->ij", vPik, b, optimize=True)    # Eq. K_2
     return J, K
 
 
@@ -106,10 +107,10 @@ def ao2mo_active(Bp: np.ndarray, n: int, C_a: np.ndarray, l0: int = 0, l1: int |
     mveri = np.zeros((n, a, a, a))
     for _, _, b in p_blocks(Bp, n, l0, l1):
         bmv = b @ C_a                                    # Eq. ao2mo_1
-        buv = np.einsum("mu,Pmv->Puv", C_a, bmv)         # Eq. ao2mo_2
+        buv = np.einsum("mu,Pmv->Puv", C_a, bmv, optimize=True)  # Eq. ao2mo_2
         nb = b.shape[0]
         eri += (buv.reshape(nb, a * a).T @ buv.reshape(nb, a * a)).reshape(a, a, a, a)  # ppaa
-        mveri += np.einsum("Pmv,Pwx->mvwx", bmv, buv)
+        mveri += np.einsum("Pmv,Pwx->mvwx", bmv, buv, optimize=True)
     return eri, mveri
 
 
@@ -124,7 +125,7 @@ def df_transform(Bp: np.ndarray, n: int, C: np.ndarray, act: tuple[int, int],
     lpu = np.zeros((naux, p1 - p0, a))
     for l0, l1, b in p_blocks(Bp, n):
         lmu[l0:l1] = b @ C_a
-        lpu[l0:l1] = np.einsum("mp,Pmu->Ppu", C[:, p0:p1], lmu[l0:l1])
+        lpu[l0:l1] = np.einsum("mp,Pmu->Ppu", C[:, p0:p1], lmu[l0:l1], optimize=True)
     return lmu, lpu
 
 
@@ -194,7 +195,7 @@ def energy_grad(Bp: np.ndarray, n: int, h: np.ndarray, C: np.ndarray, ncore: int
         G[:, :ncore] = 4.0 * (FI + FA) @ C_c
         if a:
             G[:, ncore:ncore + a] = 2.0 * FI @ C_a @ Dact + 2.0 * np.einsum(
-                "mvwx,uvwx->mu", mveri, Gact)
+                "mvwx,uvwx->mu", mveri, Gact, optimize=True)
         CtG = C.T @ G
         out.update(G=G, Fgen=0.5 * CtG, gorb=CtG - CtG.T)
     return out
