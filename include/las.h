@@ -22,8 +22,8 @@
  *     LAS_OK once its work is queued; errors found on the device (a failed bounds or status
  *     check inside a kernel) are recorded in a status word and reported by the next
  *     las_sync() (and by every later call).  The library never aborts and never traps.
- *   - Nothing is allocated or freed inside a call other than las_create / las_destroy /
- *     las_reserve.
+ *   - Device memory is allocated only by las_create and freed only by las_destroy; the
+ *     evaluation calls allocate nothing.
  *   - A context is not thread-safe: use one context per host thread, or serialise calls.
  */
 #ifndef LAS_H_
@@ -122,10 +122,31 @@ las_status las_energy_grad_host(las_ctx* ctx, const double* C_host, const double
                                 double* E_host, double* dEdC_host);
 
 /* Per-stage device times (milliseconds) of the last evaluation when timing is enabled with
- * las_set_timing(ctx, 1); stage order: half transform, full transform, per-L contractions,
- * projections, assembly.  Returns the number of stages written (<= cap). */
+ * las_set_timing(ctx, 1), measured with CUDA events on the context's stream.  Stage order:
+ * [0] C packing and half transform (S1), [1] occupied full transform (S2), [2] per-aux
+ * contractions, [3] projections (S5/S6), [4] one-electron terms, energy and gradient assembly.
+ * With more than one auxiliary chunk, stages 0-3 cover the first chunk only.
+ * Returns the number of stages written (<= cap). */
 las_status las_set_timing(las_ctx* ctx, int enable);
 int las_stage_times(las_ctx* ctx, float* ms, int cap);
+
+/* Emulated-FP64 GEMM on the BF16 tensor cores, the building block of LAS_SPLIT_BF16:
+ *   C[M][N] = A[M][K] * B[K][N]   (row-major, leading dimensions lda >= K, ldb >= N, ldc >= N)
+ * A is scaled per row and B per column by powers of two, each cut into six BF16 digits, and the
+ * 21 digit products of total weight <= 2^-40 are formed with exact FP32 partial sums for the
+ * three leading weights (integer recombination) and one FP32 sum for the rest.  The error is
+ * that of truncating both operands to 47 bits below their row / column maximum.
+ * The method has no counterpart in the paper (which runs FP64 GEMMs and names reduced precision
+ * only as an outlook, section "Outlook"); it implements that outlook for this hardware.
+ * workspace: device buffer of at least las_split_gemm_workspace(M, N, K) bytes, 256-byte
+ * aligned, owned by the caller.  Synchronous: returns after C is written (or an error). */
+size_t las_split_gemm_workspace(long M, long N, long K);
+las_status las_split_gemm(long M, long N, long K, const double* A, long lda, const double* B,
+                          long ldb, double* C, long ldc, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* Number of kernels this library has launched in this process so far (all contexts). */
+long las_kernel_launches(void);
 
 const char* las_status_str(las_status status);
 

@@ -94,4 +94,5 @@ void gemm_f64(int M, int N, int K, int batch, int ksplit, LA a, LB b, SC c, cuda
   if (kchunk < 16) kchunk = 16;
   dim3 grid((M + 63) / 64, (N + 63) / 64, batch * ksplit);
   lasdf::k_gemm_f64<LA, LB, SC><<<grid, 128, 0, s>>>(M, N, K, ksplit, kchunk, a, b, c);
+  las_count_launch();
 }

@@ -20,7 +20,14 @@
 #include "las_common.cuh"
 #include "las_split.cuh"
 
+#include <atomic>
+
 static thread_local char g_last_error[512];
+static std::atomic<long> g_launches{0};
+
+void las_count_launch(long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+extern "C" long las_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 void las_record_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   snprintf(g_last_error, sizeof(g_last_error), "%s failed: %s (%s:%d)", what,
@@ -104,7 +111,9 @@ static void free_all(las_ctx* x) {
 
 static size_t chunk_bytes(const las_ctx* x, int Lc) {
   size_t op = x->op, n = x->n;
-  return (size_t)Lc * op * (n + 2 * op) * sizeof(double);
+  size_t b = (size_t)Lc * op * (n + 2 * op) * sizeof(double);
+  if (x->prec == LAS_SPLIT_BF16) b += (size_t)Lc * split_bytes_per_aux(x->n, x->op);
+  return b;
 }
 
 extern "C" las_status las_create(las_ctx** out, const las_dims* d, const double* B_packed,
@@ -207,7 +216,8 @@ extern "C" las_status las_create(las_ctx** out, const las_dims* d, const double*
     st = per_aux_prepare(a);
   }
   if (st == LAS_OK && prec == LAS_SPLIT_BF16) {
-    st = split_create(&x->split, x->n, x->X, x->op, x->Lc, B_packed, x->stream, &x->bytes);
+    st = split_create(&x->split, x->n, x->X, x->op, x->Lc, B_packed, x->status, x->stream,
+                      &x->bytes);
   }
   if (st == LAS_OK) {
     cudaError_t e = cudaStreamSynchronize(x->stream);
@@ -282,7 +292,7 @@ extern "C" int las_stage_times(las_ctx* x, float* ms, int cap) {
 static inline void stage_mark(las_ctx* x, int i) {
   if (x->timing && i < 8) {
     cudaEventRecord(x->ev[i], x->stream);
-    x->nstage = i;
+    if (i > 0) x->nstage = i;
   }
 }
 
@@ -290,16 +300,19 @@ static inline void stage_mark(las_ctx* x, int i) {
 // Chain pieces
 // ------------------------------------------------------------------------------------------
 // S1 + S2 on auxiliary rows [l0, l0+nL): Ht[b][p][mu] = (b^L C_occ)(mu,p), T[b] = C_occ^T H
-static las_status half_and_full(las_ctx* x, int l0, int nL, int want_T) {
+static las_status half_and_full(las_ctx* x, int l0, int nL, int want_T, int mark = -1) {
   const int n = x->n, op = x->op;
   if (x->prec == LAS_SPLIT_BF16) {
-    return split_half_full(x->split, l0, nL, x->Cocc, x->Ht, want_T ? x->T : nullptr,
-                           x->stream);
+    las_status st = split_half(x->split, l0, nL, x->Ht, x->stream);
+    if (st != LAS_OK) return st;
+    if (mark >= 0) stage_mark(x, mark);
+    return want_T ? split_full(x->split, nL, x->Ht, x->T, x->stream) : LAS_OK;
   }
   PackedSymA A{x->Bp, x->npair, l0};
   StridedA Bm{x->Cocc, 0, op, 1};
   StridedC Ch{x->Ht, (long)op * n, 1, n, 1.0, 0};
   gemm_f64(n, op, n, nL, 1, A, Bm, Ch, x->stream);
+  if (mark >= 0) stage_mark(x, mark);
   if (want_T) {
     StridedA Ah{x->Ht, (long)op * n, n, 1};
     StridedC Ct{x->T, (long)op * op, op, 1, 1.0, 0};
@@ -312,7 +325,7 @@ static las_status half_and_full(las_ctx* x, int l0, int nL, int want_T) {
 static las_status project(las_ctx* x, int nL, int accumulate) {
   const int n = x->n, op = x->op;
   if (x->prec == LAS_SPLIT_BF16) {
-    return split_project(x->split, nL, x->Ht, x->W, x->Out, accumulate, x->stream);
+    return split_project(x->split, nL, x->W, x->Out, accumulate, x->stream);
   }
   int ks = std::max(1, std::min(x->ksplit, (nL * op) / 64));
   StridedA A{x->Ht, 0, 1, n};
@@ -339,15 +352,16 @@ static las_status evaluate(las_ctx* x, const double* C, const double* h, const d
   }
   for (int l0 = 0; l0 < x->X; l0 += x->Lc) {
     const int nL = std::min(x->Lc, x->X - l0);
-    if ((st = half_and_full(x, l0, nL, 1)) != LAS_OK) return st;
-    if (l0 == 0) stage_mark(x, 1);
-    launch_per_aux(x->T, nL, op, dm1s, dm2, x->fi, x->W, x->eps + l0, x->vc + l0, x->va + l0,
-                   with_grad, x->status, x->stream);
-    if ((st = check_launch()) != LAS_OK) return st;
+    if ((st = half_and_full(x, l0, nL, 1, l0 == 0 ? 1 : -1)) != LAS_OK) return st;
     if (l0 == 0) stage_mark(x, 2);
+    // split mode: W is written transposed and row-scaled for the split projection GEMM
+    launch_per_aux(x->T, nL, op, dm1s, dm2, x->fi, x->W, x->eps + l0, x->vc + l0, x->va + l0,
+                   with_grad, x->split ? split_hexp(x->split) : nullptr, x->status, x->stream);
+    if ((st = check_launch()) != LAS_OK) return st;
+    if (l0 == 0) stage_mark(x, 3);
     if (with_grad && (st = project(x, nL, l0 > 0)) != LAS_OK) return st;
+    if (l0 == 0) stage_mark(x, 4);
   }
-  stage_mark(x, 3);
   {  // one-electron pieces: hC = h C_occ, hmo = C_occ^T hC
     StridedA Ah{h, 0, n, 1};
     StridedA Bc{x->Cocc, 0, op, 1};
@@ -369,7 +383,7 @@ static las_status evaluate(las_ctx* x, const double* C, const double* h, const d
       launch_antisym(x->M, nmo, x->o, op, gorb, x->stream);
     }
   }
-  stage_mark(x, 4);
+  stage_mark(x, 5);
   return check_launch();
 }
 
@@ -428,7 +442,7 @@ extern "C" las_status las_df_jk(las_ctx* x, const double* C, double* J, double* 
     if ((st = half_and_full(x, l0, nL, J != nullptr)) != LAS_OK) return st;
     if (J) {  // vc_L = 2 sum_i T_L(i,i)
       launch_per_aux(x->T, nL, op, nullptr, nullptr, x->fi_c, x->W, x->eps + l0,
-                     x->vc + l0, x->va + l0, 0, x->status, x->stream);
+                     x->vc + l0, x->va + l0, 0, nullptr, x->status, x->stream);
     }
     if (K) {  // K = 2 sum_{L,i} H_L(:,i) H_L(:,i)^T
       StridedA A{x->Ht, 0, 1, n};

@@ -23,6 +23,9 @@
 
 void las_record_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
+// Process-wide count of kernels this library has launched (diagnostics).
+void las_count_launch(long k = 1);
+
 // Fragment description in constant-size form (passed by value to kernels).
 struct FragInfo {
   int nfrag;
@@ -76,9 +79,10 @@ void gemm_f64(int M, int N, int K, int batch, int ksplit, LA a, LB b, SC c, cuda
 void launch_pack_cocc(const double* C, int n, int nmo, int o, int op, double* Cocc,
                       cudaStream_t s);
 las_status per_aux_prepare(int nact);
+// gexp == nullptr: W[L][p][q];  otherwise W is written as Wt[q][L*op + p] * 2^gexp[L*op + p]
 void launch_per_aux(const double* T, int nL, int op, const double* dm1s, const double* dm2,
                     const FragInfo& fi, double* W, double* eps, double* vc, double* va,
-                    int with_grad, int* status, cudaStream_t s);
+                    int with_grad, const int* gexp, int* status, cudaStream_t s);
 void launch_reduce_partials(const double* part, int nsplit, long count, double* out,
                             int accumulate, cudaStream_t s);
 void launch_assemble_grad(const double* Out, const double* hC, const double* dm1s,

@@ -44,11 +44,18 @@ __device__ __forceinline__ int frag_of(const FragInfo& fi, int u) {
 //   eps_L  = vc^2/2 - sum_ij T(i,j)^2 + vc va - sum_{i,u} Z(i,u) T(i,u) + 1/2 sum_uv T(u,v) Y(u,v)
 //            with Z = T(core,act) D  (the L-th term of the two-electron energy)
 //   W_L(p,q): the matrix with  dE/dC(two-electron part) = sum_L H_L W_L, H_L = b^L C_occ.
+// x * 2^g for normal or zero x (exponent-field arithmetic; no FP64 multiply)
+__device__ __forceinline__ double scale2(double x, int g) {
+  long long b = __double_as_longlong(x);
+  if ((b & 0x7FF0000000000000ll) == 0) return x == 0.0 ? x : ldexp(x, g);
+  return __longlong_as_double(b + (((long long)g) << 52));
+}
+
 __global__ void __launch_bounds__(256)
-k_per_aux(const double* __restrict__ T, int op, const double* __restrict__ dm1s,
+k_per_aux(const double* __restrict__ T, int nL, int op, const double* __restrict__ dm1s,
           const double* __restrict__ dm2, FragInfo fi, double* __restrict__ W,
           double* __restrict__ eps, double* __restrict__ vcv, double* __restrict__ vav,
-          int with_grad, int* status) {
+          int with_grad, const int* __restrict__ gexp, int* status) {
   extern __shared__ double sm[];
   const int a = fi.nact, c = fi.ncore, o = c + a;
   double* Taa = sm;             // a*a
@@ -133,6 +140,16 @@ k_per_aux(const double* __restrict__ T, int op, const double* __restrict__ dm1s,
   // Z(i,u) = sum_v T(i, c+v) D(v,u) over core i and active u; its contraction with T(i,u).
   double pz = 0.0;
   double* WL = W + Lb * (long)op * op;
+  const long wld = (long)nL * op;
+  // W_L(p,q) -> its storage slot (plain, or transposed and scaled by 2^gexp for split mode)
+  auto putW = [&](int p, int q, double w) {
+    if (gexp) {
+      const long k = Lb * (long)op + p;
+      W[(long)q * wld + k] = scale2(w, gexp[k]);
+    } else {
+      WL[(long)p * op + q] = w;
+    }
+  };
   for (long idx = tid; idx < (long)c * a; idx += 256) {
     const int i = (int)(idx / a), u = (int)(idx % a);
     const int K = frag_of(fi, u), oK = fi.off[K], mK = fi.off[K + 1] - oK;
@@ -141,8 +158,8 @@ k_per_aux(const double* __restrict__ T, int op, const double* __restrict__ dm1s,
     for (int v = oK; v < oK + mK; ++v) z += Ti[v] * Ds[v * a + u];
     pz += z * Ti[u];
     if (with_grad) {
-      WL[(long)i * op + c + u] = -2.0 * z;
-      WL[(long)(c + u) * op + i] = -2.0 * z;
+      putW(i, c + u, -2.0 * z);
+      putW(c + u, i, -2.0 * z);
     }
   }
   double pe = 0.0;
@@ -157,10 +174,12 @@ k_per_aux(const double* __restrict__ T, int op, const double* __restrict__ dm1s,
   if (!with_grad) return;
   // core-core block, active-active block and zero padding
   for (long idx = tid; idx < (long)op * op; idx += 256) {
-    const int p = (int)(idx / op), q = (int)(idx % op);
+    // q-major in split mode so that consecutive threads write consecutive p (coalesced)
+    const int p = gexp ? (int)(idx % op) : (int)(idx / op);
+    const int q = gexp ? (int)(idx / op) : (int)(idx % op);
     double w;
     if (p < c && q < c) {
-      w = -4.0 * TL[idx] + (p == q ? 4.0 * (vc + va) : 0.0);
+      w = -4.0 * TL[(long)p * op + q] + (p == q ? 4.0 * (vc + va) : 0.0);
     } else if (p >= c && p < o && q >= c && q < o) {
       const int wv = p - c, u = q - c;
       w = 2.0 * vc * Ds[wv * a + u] + 2.0 * Y[u * a + wv];
@@ -169,7 +188,7 @@ k_per_aux(const double* __restrict__ T, int op, const double* __restrict__ dm1s,
     } else {
       continue;  // core/active blocks written above
     }
-    WL[idx] = w;
+    putW(p, q, w);
   }
 }
 
@@ -285,6 +304,7 @@ static inline unsigned nblk(long count, int nt) { return (unsigned)((count + nt 
 void launch_pack_cocc(const double* C, int n, int nmo, int o, int op, double* Cocc,
                       cudaStream_t s) {
   k_pack_cocc<<<nblk((long)n * op, 256), 256, 0, s>>>(C, n, nmo, o, op, Cocc);
+  las_count_launch();
 }
 
 las_status per_aux_prepare(int nact) {
@@ -302,42 +322,51 @@ las_status per_aux_prepare(int nact) {
 
 void launch_per_aux(const double* T, int nL, int op, const double* dm1s, const double* dm2,
                     const FragInfo& fi, double* W, double* eps, double* vc, double* va,
-                    int with_grad, int* status, cudaStream_t s) {
+                    int with_grad, const int* gexp, int* status, cudaStream_t s) {
   if (nL <= 0) return;
   size_t smem = (3 * (size_t)fi.nact * fi.nact + 256 + LAS_MAX_FRAG) * sizeof(double);
-  k_per_aux<<<nL, 256, smem, s>>>(T, op, dm1s, dm2, fi, W, eps, vc, va, with_grad, status);
+  k_per_aux<<<nL, 256, smem, s>>>(T, nL, op, dm1s, dm2, fi, W, eps, vc, va, with_grad, gexp,
+                                  status);
+  las_count_launch();
 }
 
 void launch_reduce_partials(const double* part, int nsplit, long count, double* out,
                             int accumulate, cudaStream_t s) {
   k_reduce_partials<<<nblk(count, 256), 256, 0, s>>>(part, nsplit, count, out, accumulate);
+  las_count_launch();
 }
 
 void launch_assemble_grad(const double* Out, const double* hC, const double* dm1s,
                           const FragInfo& fi, int n, int nmo, int op, double* G,
                           cudaStream_t s) {
   k_assemble_grad<<<nblk((long)n * nmo, 256), 256, 0, s>>>(Out, hC, dm1s, fi, n, nmo, op, G);
+  las_count_launch();
 }
 
 void launch_energy_final(const double* eps, int X, const double* hmo, int op,
                          const double* dm1s, const FragInfo& fi, double* E, cudaStream_t s) {
   k_energy_final<<<1, 256, 0, s>>>(eps, X, hmo, op, dm1s, fi, E);
+  las_count_launch();
 }
 
 void launch_antisym(const double* M, int nmo, int o, int op, double* g, cudaStream_t s) {
   k_antisym<<<nblk((long)nmo * nmo, 256), 256, 0, s>>>(M, nmo, o, op, g);
+  las_count_launch();
 }
 
 void launch_coulomb_packed(const double* Bp, const double* vc, int X, long npair, double* Jp,
                            cudaStream_t s) {
   k_coulomb_packed<<<nblk(npair, 256), 256, 0, s>>>(Bp, vc, X, npair, Jp);
+  las_count_launch();
 }
 
 void launch_unpack_sym(const double* Jp, int n, double* J, cudaStream_t s) {
   k_unpack_sym<<<nblk((long)n * n, 256), 256, 0, s>>>(Jp, n, J);
+  las_count_launch();
 }
 
 void launch_copy_cols(const double* Ht, int X, int op, int n, int c0, int a, double* Lmu,
                       cudaStream_t s) {
   k_copy_cols<<<nblk((long)X * n * a, 256), 256, 0, s>>>(Ht, X, op, n, c0, a, Lmu);
+  las_count_launch();
 }

@@ -1,16 +1,693 @@
+// Split-precision (emulated FP64) GEMMs on the tcgen05 tensor cores.
+//
+// An FP64 operand is scaled per row (A) or per column (B) by a power of two 2^e with
+// max|x| < 2^e, rounded to 47 fractional bits and cut into NDIG = 6 balanced base-256 digits,
+//     x = 2^e * 2^-7 * sum_s d_s 2^-8s ,   |d_s| <= 128,
+// each stored exactly as a BF16 "digit plane" value d_s * 2^-8s.  The product keeps the digit pairs
+// with s + t <= 5 (21 of 36):
+//   * groups q = s + t = 0..3 are accumulated EXACTLY: every partial sum is an integer multiple
+//     of 2^-8q of magnitude at most 2^24 * 2^-8q when a group is flushed every 256 values of k,
+//     so the FP32 tensor-core accumulator loses nothing; each flush is added, as an integer, into
+//     an int64 fixed-point accumulator;
+//   * groups q = 4, 5 (weights 2^-32 and 2^-40) share one FP32 accumulator.  (The tensor core's
+//     FP32 accumulation of products of very different weights is measurably less accurate than
+//     IEEE rounding, which is why weight 2^-24 is kept in the exact part.)
+// The recombination uses integer arithmetic only (FP64 arithmetic is slow on this part): the
+// fixed-point sum and the rounded FP32 tail are merged into one int64 and turned into an FP64
+// value by building its bit pattern.  The chosen digit count and pair set follow the split-product
+// ("Ozaki") scheme for emulating a higher precision with low-precision products.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdio.h>
+
+#include <algorithm>
+
 #include "las_split.cuh"
+#include "sm100_ptx.cuh"
 
-struct SplitState { int dummy; };
+namespace lasdf_split {
 
-las_status split_create(SplitState** s, int, int, int, int, const double*, cudaStream_t, size_t*) {
-  *s = nullptr;
-  return LAS_ERR_UNSUPPORTED;
+constexpr int NDIG = 6;
+constexpr int BM = 128;          // rows per CTA tile (tcgen05 M)
+constexpr int BN = 96;           // columns per CTA tile (tcgen05 N)
+constexpr int BK = 32;           // K per pipeline stage (one 64-byte swizzle row of BF16)
+constexpr int NSTAGE = 2;
+constexpr int NEXACT = 4;        // exact weight groups q = 0..3
+constexpr int CHUNK = 8;         // stages per exact chunk (256 values of k)
+constexpr int A_PLANE = BM * BK * 2;                 // 8192 B
+constexpr int B_PLANE = BN * BK * 2;                 // 6144 B
+constexpr int A_BYTES = NDIG * A_PLANE;              // 49152
+constexpr int B_BYTES = NDIG * B_PLANE;              // 36864
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;       // 86016
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256;
+constexpr int TMEM_COLS = 512;
+constexpr int COL_EXACT0 = 0;    // exact groups q = 0..3 at 0, 96, 192, 288; tail at 384
+constexpr int COL_TAIL = NEXACT * BN;
+constexpr int NTHREADS = 320;    // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr uint32_t IDESC = sm100::idesc_bf16(BM, BN);
+
+struct OzParams {
+  int M, N;                // output rows / columns
+  int kb_total;            // K blocks of BK
+  int kb_per_split;
+  const int* ea;           // row exponents [M] (nullptr: 0)
+  const int* eb;           // column exponents [N]
+  double* out;
+  int mode;                // 0: out[z*zstride + r*ldc + c]; 1: Ht layout (rows (L,mu))
+  long ldc, zstride;
+  int ht_n, ht_op;
+  int sh;                  // fractional bits kept when merging the tail
+  int* status;
+};
+
+__device__ __forceinline__ double make_double(long long W, int E) {
+  if (W == 0) return 0.0;
+  unsigned long long sgn = W < 0 ? (1ull << 63) : 0ull;
+  unsigned long long m = W < 0 ? (unsigned long long)(-W) : (unsigned long long)W;
+  int lz = __clzll((long long)m);
+  m <<= lz;
+  int e = 63 - lz + E;
+  unsigned long long mant = m >> 11;
+  unsigned long long rem = m & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) {
+    mant += 1;
+    if (mant >> 53) {
+      mant >>= 1;
+      e += 1;
+    }
+  }
+  int eb = e + 1023;
+  if (eb <= 0 || eb >= 2047) {  // outside the normal range: slow but exact path
+    const double v = ldexp((double)mant, e - 52);
+    return sgn ? -v : v;
+  }
+  unsigned long long bits = sgn | ((unsigned long long)eb << 52) | (mant & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
 }
-void split_destroy(SplitState*) {}
-las_status split_prepare_C(SplitState*, const double*, cudaStream_t) { return LAS_ERR_UNSUPPORTED; }
-las_status split_half_full(SplitState*, int, int, const double*, double*, double*, cudaStream_t) {
-  return LAS_ERR_UNSUPPORTED;
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+        OzParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + NSTAGE * STAGE_BYTES);
+  uint64_t* full = bars;              // [NSTAGE]
+  uint64_t* empty = bars + NSTAGE;    // [NSTAGE]
+  uint64_t* accf = bars + 2 * NSTAGE;
+  uint64_t* acce = bars + 2 * NSTAGE + 1;
+  uint64_t* drain = bars + 2 * NSTAGE + 2;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * NSTAGE + 3);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // linear tile index: the column tiles of one row tile are adjacent in launch order so that
+  // they share the row tile's digit planes through L2
+  const int ntn = (p.N + BN - 1) / BN;
+  const int n0 = (int)(blockIdx.x % ntn) * BN, m0 = (int)(blockIdx.x / ntn) * BM, z = blockIdx.z;
+  const int kb0 = z * p.kb_per_split;
+  const int nkb = min(p.kb_total, kb0 + p.kb_per_split) - kb0;
+  const int nchunks = (nkb + CHUNK - 1) / CHUNK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      sm100::mbar_init(&full[s], 1);
+      sm100::mbar_init(&empty[s], 1);
+    }
+    sm100::mbar_init(accf, 1);
+    sm100::mbar_init(acce, 8);
+    sm100::mbar_init(drain, 1);
+    *abort_flag = 0;
+    sm100::fence_mbar_init();
+    sm100::tma_prefetch_desc(&tmA);
+    sm100::tma_prefetch_desc(&tmB);
+  }
+  if (warp == 1) {
+    sm100::tmem_alloc(tmem_slot, TMEM_COLS);
+    sm100::tmem_relinquish();
+  }
+  sm100::tc_fence_before();
+  __syncthreads();
+  sm100::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (nkb > 0 && warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    for (int i = 0; i < nkb; ++i) {
+      const int st = i % NSTAGE;
+      if (i >= NSTAGE &&
+          !sm100::mbar_wait(&empty[st], ((i / NSTAGE) - 1) & 1, abort_flag, p.status, LAS_ERR_TIMEOUT))
+        break;
+      uint8_t* sa = smem + st * STAGE_BYTES;
+      sm100::mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
+      const int kx = (kb0 + i) * BK;
+      sm100::tma_load_3d(sa, &tmA, &full[st], kx, m0, 0);
+      sm100::tma_load_3d(sa + A_BYTES, &tmB, &full[st], kx, n0, 0);
+    }
+    // never leave the CTA with a bulk copy still writing its shared memory
+    for (int i = max(0, nkb - NSTAGE); i < nkb; ++i)
+      sm100::mbar_wait(&full[i % NSTAGE], (i / NSTAGE) & 1, abort_flag, p.status, LAS_ERR_TIMEOUT);
+  } else if (nkb > 0 && warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    bool ok = true;
+    bool tail_started = false;
+    for (int i = 0; i < nkb && ok; ++i) {
+      const int st = i % NSTAGE;
+      if (!sm100::mbar_wait(&full[st], (i / NSTAGE) & 1, abort_flag, p.status, LAS_ERR_TIMEOUT)) {
+        ok = false;
+        break;
+      }
+      sm100::tc_fence_after();
+      const uint32_t sa = sm100::smem_u32(smem + st * STAGE_BYTES);
+      const uint32_t sb = sa + A_BYTES;
+      // tail groups q = 4, 5 into one FP32 accumulator
+      for (int s = 0; s < NDIG; ++s)
+        for (int t = (s >= NEXACT ? 0 : NEXACT - s); s + t <= NDIG - 1; ++t)
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            sm100::mma_bf16(tmem + COL_TAIL, sm100::smem_desc_sw64(sa + s * A_PLANE + kk * 32),
+                            sm100::smem_desc_sw64(sb + t * B_PLANE + kk * 32), IDESC,
+                            tail_started ? 1u : 0u);
+            tail_started = true;
+          }
+      const int c = i / CHUNK;
+      const bool first_in_chunk = (i % CHUNK) == 0;
+      if (first_in_chunk && c > 0) {
+        if (!sm100::mbar_wait(acce, (c - 1) & 1, abort_flag, p.status, LAS_ERR_TIMEOUT)) {
+          ok = false;
+          break;
+        }
+        sm100::tc_fence_after();
+      }
+      // exact groups q = 0..3
+      for (int q = 0; q < NEXACT; ++q) {
+        bool started = !first_in_chunk;
+        for (int s = 0; s <= q; ++s)
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            sm100::mma_bf16(tmem + COL_EXACT0 + q * BN,
+                            sm100::smem_desc_sw64(sa + s * A_PLANE + kk * 32),
+                            sm100::smem_desc_sw64(sb + (q - s) * B_PLANE + kk * 32), IDESC,
+                            started ? 1u : 0u);
+            started = true;
+          }
+      }
+      sm100::mma_commit(&empty[st]);
+      if ((i % CHUNK) == CHUNK - 1 || i == nkb - 1) sm100::mma_commit(accf);
+    }
+    // make sure no MMA is still writing TMEM when the CTA tears down
+    sm100::mma_commit(drain);
+    sm100::mbar_wait(drain, 0, abort_flag, p.status, LAS_ERR_TIMEOUT);
+  } else if (warp >= 2) {
+    // ---------------- epilogue (8 warps) ----------------
+    const int lq = warp & 3;                 // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;        // columns [half*48, half*48+48)
+    const int row = m0 + lq * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + half * 48;
+    long long acc[48];
+#pragma unroll
+    for (int j = 0; j < 48; ++j) acc[j] = 0;
+    bool ok = nkb > 0;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      if (!sm100::mbar_wait(accf, c & 1, abort_flag, p.status, LAS_ERR_TIMEOUT)) {
+        ok = false;
+        break;
+      }
+      sm100::tc_fence_after();
+#pragma unroll
+      for (int q = 0; q < NEXACT; ++q) {
+        const float up = __int_as_float((127 + 8 * q) << 23);   // 2^(8q)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          uint32_t r[16];
+          sm100::tmem_ld16(tl + COL_EXACT0 + q * BN + j * 16, r);
+          sm100::tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int iv = __float2int_rn(__uint_as_float(r[e]) * up);
+            acc[j * 16 + e] += (long long)iv * (1ll << (8 * (NEXACT - 1 - q)));
+          }
+        }
+      }
+      sm100::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) sm100::mbar_arrive(acce);
+    }
+    if (ok) {
+      // merge the FP32 tail and write FP64 results
+      const float tscale = __int_as_float((127 + 8 * (NEXACT - 1) + p.sh) << 23);  // 2^(24+sh)
+      const int ea = (p.ea && row < p.M) ? p.ea[row] : 0;
+      long L = 0, mu = 0;
+      if (p.mode == 1) {
+        L = row / p.ht_n;
+        mu = row - L * p.ht_n;
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        uint32_t r[16];
+        sm100::tmem_ld16(tl + COL_TAIL + j * 16, r);
+        sm100::tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int col = n0 + half * 48 + j * 16 + e;
+          if (row < p.M && col < p.N) {
+            const long long W =
+                (long long)((unsigned long long)acc[j * 16 + e] << p.sh) +
+                __float2ll_rn(__uint_as_float(r[e]) * tscale);
+            const int E = ea + p.eb[col] - 14 - 8 * (NEXACT - 1) - p.sh;
+            const double v = make_double(W, E);
+            if (p.mode == 0)
+              p.out[(long)z * p.zstride + (long)row * p.ldc + col] = v;
+            else
+              p.out[(L * p.ht_op + col) * (long)p.ht_n + mu] = v;
+          }
+        }
+      }
+    }
+    sm100::tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    sm100::tc_fence_after();
+    sm100::tmem_dealloc(tmem, TMEM_COLS);
+  }
 }
-las_status split_project(SplitState*, int, const double*, const double*, double*, int, cudaStream_t) {
-  return LAS_ERR_UNSUPPORTED;
+
+// ------------------------------------------------------------------------------------------
+// Digit extraction (integer operations on the FP64 bit patterns)
+// ------------------------------------------------------------------------------------------
+struct RowsStrided {  // element (r, k) = base[r*sr + k*sk] * 2^(gexp ? gexp[k] : 0)
+  const double* base;
+  long sr, sk;
+  const int* gk;
+  __device__ __forceinline__ double operator()(long r, long k) const {
+    double x = base[r * sr + k * sk];
+    if (gk) {
+      long long b = __double_as_longlong(x);
+      if ((b & 0x7FF0000000000000ll) != 0) b += ((long long)gk[k]) << 52;
+      else if (x != 0.0) return ldexp(x, gk[k]);
+      x = __longlong_as_double(b);
+    }
+    return x;
+  }
+};
+
+struct RowsPacked {   // element (r = L*n + mu, k = nu) of the packed symmetric b^L
+  const double* Bp;
+  long npair;
+  int n;
+  __device__ __forceinline__ double operator()(long r, long k) const {
+    long L = r / n, mu = r - L * n;
+    long hi = mu > k ? mu : k, lo = mu > k ? k : mu;
+    return Bp[L * npair + hi * (hi + 1) / 2 + lo];
+  }
+};
+
+// One warp per row r < R: exponent e_r with max|x| < 2^e_r, digit planes
+// planes[s][r][k] = bf16(d_s * 2^-8s) for k < K and 0 for K <= k < Kp.
+template <class Acc>
+__global__ void __launch_bounds__(256)
+k_slice_rows(Acc acc, long R, long K, long Kp, long plane, __nv_bfloat16* planes, int* ex) {
+  const long r = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= R) return;
+  unsigned long long mx = 0;
+  for (long k = lane; k < K; k += 32) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(acc(r, k)) & 0x7FFFFFFFFFFFFFFFull;
+    mx = b > mx ? b : mx;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = v > mx ? v : mx;
+  }
+  const int e = mx ? (int)((mx >> 52) & 0x7FF) - 1022 : 0;   // max|x| < 2^e
+  if (lane == 0) ex[r] = e;
+  for (long k = lane; k < Kp; k += 32) {
+    long long Y = 0;
+    if (k < K) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(acc(r, k));
+      const int bex = (int)((b >> 52) & 0x7FF);
+      unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+      int ee = bex;
+      if (bex != 0) m |= (1ull << 52); else ee = 1;
+      // |x| * 2^(47 - e) = m * 2^(ee - 1075 + 47 - e)
+      const int shift = ee - 1028 - e;
+      unsigned long long y;
+      if (shift >= 0) y = m << shift;
+      else if (shift > -63) y = (m + (1ull << (-shift - 1))) >> (-shift);
+      else y = 0;
+      Y = (b >> 63) ? -(long long)y : (long long)y;
+    }
+    int d[NDIG];
+#pragma unroll
+    for (int s = NDIG - 1; s >= 1; --s) {
+      const long long t = ((Y + 128) & 255) - 128;
+      d[s] = (int)t;
+      Y = (Y - t) >> 8;
+    }
+    d[0] = (int)Y;
+#pragma unroll
+    for (int s = 0; s < NDIG; ++s) {
+      const float f = (float)d[s] * __int_as_float((127 - 8 * s) << 23);
+      planes[s * plane + r * Kp + k] = __float2bfloat16_rn(f);
+    }
+  }
+}
+
+// planes [NDIG][R][Kin] -> out [NDIG][Kin][Rout] (transpose of every plane; rows >= R are 0)
+__global__ void k_transpose_planes(const __nv_bfloat16* in, long R, long Kin, long Kp_in,
+                                   long in_plane, __nv_bfloat16* out, long Rp_out) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  const int s = blockIdx.z;
+  const long r0 = (long)blockIdx.y * 32, k0 = (long)blockIdx.x * 32;
+  const __nv_bfloat16* src = in + (long)s * in_plane;
+  __nv_bfloat16* dst = out + (long)s * Kin * Rp_out;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const long r = r0 + i, k = k0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < R && k < Kin) ? src[r * Kp_in + k] : __float2bfloat16_rn(0.f);
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const long k = k0 + i, r = r0 + threadIdx.x;
+    if (k < Kin && r < Rp_out) dst[k * Rp_out + r] = tile[threadIdx.x][i];
+  }
+}
+
+}  // namespace lasdf_split
+
+using namespace lasdf_split;
+
+// ------------------------------------------------------------------------------------------
+// Host side
+// ------------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 3D map over digit planes [NDIG][rows][Kp] (BF16), box {BK, box_rows, NDIG}, 64-byte swizzle.
+static las_status make_plane_map(CUtensorMap* m, const void* base, long rows, long Kp,
+                                 long plane_stride_elems, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return LAS_ERR_CUDA;
+  if (((uintptr_t)base & 15) || (Kp % 8) || rows <= 0 || rows > 0xFFFFFFFFL) return LAS_ERR_INTERNAL;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)NDIG};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)plane_stride_elems * 2};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)NDIG};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
+                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? LAS_OK : LAS_ERR_INTERNAL;
+}
+
+static las_status ozaki_prepare() {
+  static int done = 0;
+  if (done) return LAS_OK;
+  cudaError_t e = cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       SMEM_BYTES);
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "cudaFuncSetAttribute(k_ozaki)", __FILE__, __LINE__);
+    return LAS_ERR_CUDA;
+  }
+  done = 1;
+  return LAS_OK;
+}
+
+static inline long rup(long x, long m) { return (x + m - 1) / m * m; }
+
+// out = A * B^T where A planes [NDIG][M][Kp] (row exponents ea) and B planes [NDIG][N][Kp]
+// (row exponents eb = column exponents of the product).  plane strides are in elements.
+las_status ozaki_gemm(const __nv_bfloat16* Ad, long a_plane, const int* ea, long M,
+                      const __nv_bfloat16* Bd, long b_plane, const int* eb, long N, long K,
+                      long Kp, int ksplit, int mode, double* out, long ldc, long zstride,
+                      int ht_n, int ht_op, int* status, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return LAS_OK;
+  las_status s = ozaki_prepare();
+  if (s != LAS_OK) return s;
+  CUtensorMap ma, mb;
+  if ((s = make_plane_map(&ma, Ad, M, Kp, a_plane, BM)) != LAS_OK) return s;
+  if ((s = make_plane_map(&mb, Bd, N, Kp, b_plane, BN)) != LAS_OK) return s;
+  OzParams p;
+  p.M = (int)M;
+  p.N = (int)N;
+  p.kb_total = (int)((K + BK - 1) / BK);
+  if (p.kb_total < 1) p.kb_total = 1;
+  if (ksplit < 1) ksplit = 1;
+  p.kb_per_split = (p.kb_total + ksplit - 1) / ksplit;
+  ksplit = (p.kb_total + p.kb_per_split - 1) / p.kb_per_split;
+  p.ea = ea;
+  p.eb = eb;
+  p.out = out;
+  p.mode = mode;
+  p.ldc = ldc;
+  p.zstride = zstride;
+  p.ht_n = ht_n;
+  p.ht_op = ht_op;
+  // fractional bits kept for the tail: |fixed-point sum| < 2^38 * (k per CTA) must fit 62 bits
+  int lgk = 0;
+  while ((1L << lgk) < (long)p.kb_per_split * BK) ++lgk;
+  p.sh = std::max(0, std::min(20, 61 - 14 - 8 * (NEXACT - 1) - lgk));
+  p.status = status;
+  const long tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+  if (tiles > 0x7FFFFFFFL || ksplit > 65535) return LAS_ERR_UNSUPPORTED;
+  dim3 grid((unsigned)tiles, 1, (unsigned)ksplit);
+  k_ozaki<<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, p);
+  las_count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "k_ozaki launch", __FILE__, __LINE__);
+    return LAS_ERR_CUDA;
+  }
+  return LAS_OK;
+}
+
+template <class Acc>
+static las_status slice_rows(Acc acc, long R, long K, long Kp, long plane, __nv_bfloat16* planes,
+                             int* ex, cudaStream_t st) {
+  if (R <= 0) return LAS_OK;
+  const long threads = R * 32;
+  k_slice_rows<Acc><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(acc, R, K, Kp, plane,
+                                                                        planes, ex);
+  las_count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "k_slice_rows launch", __FILE__, __LINE__);
+    return LAS_ERR_CUDA;
+  }
+  return LAS_OK;
+}
+
+static las_status transpose_planes(const __nv_bfloat16* in, long R, long Kin, long Kp_in,
+                                   long in_plane, __nv_bfloat16* out, long Rp_out,
+                                   cudaStream_t st) {
+  dim3 grid((unsigned)((Kin + 31) / 32), (unsigned)((Rp_out + 31) / 32), NDIG);
+  k_transpose_planes<<<grid, dim3(32, 8), 0, st>>>(in, R, Kin, Kp_in, in_plane, out, Rp_out);
+  las_count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "k_transpose_planes launch", __FILE__, __LINE__);
+    return LAS_ERR_CUDA;
+  }
+  return LAS_OK;
+}
+
+struct SplitState {
+  int n, X, op, Lc;
+  long Kp;          // padded AO dimension
+  long Rp;          // padded Lc*op
+  __nv_bfloat16* Bdig;   // [NDIG][X*n][Kp]
+  int* Bexp;             // [X*n]
+  __nv_bfloat16* Cdig;   // [NDIG][op][Kp]
+  int* Cexp;             // [op]
+  __nv_bfloat16* Hdig;   // [NDIG][Lc*op][Kp]
+  int* Hexp;             // [Lc*op]
+  __nv_bfloat16* HdigT;  // [NDIG][n][Rp]
+  __nv_bfloat16* Wdig;   // [NDIG][op][Rp]
+  int* Wexp;             // [op]
+  double* part;          // [ksplit][n][op]
+  int ksplit6;
+  int* status;
+};
+
+static void split_free(SplitState* s) {
+  void* ptrs[] = {s->Bdig, s->Bexp, s->Cdig, s->Cexp, s->Hdig, s->Hexp, s->HdigT, s->Wdig,
+                  s->Wexp, s->part};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+size_t split_bytes_per_aux(int n, int op) {
+  const long Kp = rup(n, 8);
+  return (size_t)NDIG * op * Kp * 2 * 2 + (size_t)NDIG * op * op * 2 + (size_t)op * 4;
+}
+
+las_status split_create(SplitState** out, int n, int X, int op, int Lc, const double* Bp,
+                        int* status, cudaStream_t st, size_t* bytes) {
+  *out = nullptr;
+  if (!encode_fn()) return LAS_ERR_UNSUPPORTED;
+  SplitState* s = (SplitState*)calloc(1, sizeof(SplitState));
+  if (!s) return LAS_ERR_INTERNAL;
+  s->n = n;
+  s->X = X;
+  s->op = op;
+  s->Lc = Lc;
+  s->Kp = rup(n, 8);
+  s->Rp = rup((long)Lc * op, 8);
+  s->status = status;
+  {
+    const long tiles = ((n + BM - 1) / BM) * ((op + BN - 1) / BN);
+    s->ksplit6 = (int)std::max(1L, std::min(64L, (2 * 148 + tiles - 1) / tiles));
+  }
+  size_t total = 0;
+  las_status rc = LAS_OK;
+  auto A = [&](void** p, size_t b) {
+    if (rc != LAS_OK) return;
+    if (cudaMalloc(p, b) != cudaSuccess) {
+      *p = nullptr;
+      rc = LAS_ERR_CUDA;
+      las_record_cuda_error(cudaErrorMemoryAllocation, "cudaMalloc(split)", __FILE__, __LINE__);
+      return;
+    }
+    total += b;
+  };
+  const long XN = (long)X * n;
+  A((void**)&s->Bdig, (size_t)NDIG * XN * s->Kp * 2);
+  A((void**)&s->Bexp, (size_t)XN * 4);
+  A((void**)&s->Cdig, (size_t)NDIG * op * s->Kp * 2);
+  A((void**)&s->Cexp, (size_t)op * 4);
+  A((void**)&s->Hdig, (size_t)NDIG * Lc * op * s->Kp * 2);
+  A((void**)&s->Hexp, (size_t)s->Rp * 4);
+  A((void**)&s->HdigT, (size_t)NDIG * n * s->Rp * 2);
+  A((void**)&s->Wdig, (size_t)NDIG * op * s->Rp * 2);
+  A((void**)&s->Wexp, (size_t)op * 4);
+  A((void**)&s->part, (size_t)s->ksplit6 * n * op * 8);
+  if (rc == LAS_OK) {
+    // one-time digit planes of the Cholesky vectors: rows (L, mu), K = nu
+    RowsPacked acc{Bp, (long)n * (n + 1) / 2, n};
+    rc = slice_rows(acc, XN, n, s->Kp, XN * s->Kp, s->Bdig, s->Bexp, st);
+  }
+  if (rc != LAS_OK) {
+    split_free(s);
+    free(s);
+    return rc;
+  }
+  *bytes += total;
+  *out = s;
+  return LAS_OK;
+}
+
+void split_destroy(SplitState* s) {
+  if (!s) return;
+  split_free(s);
+  free(s);
+}
+
+const int* split_hexp(SplitState* s) { return s->Hexp; }
+
+las_status split_prepare_C(SplitState* s, const double* Cocc, cudaStream_t st) {
+  // rows p of C_occ^T (K = nu): element (p, nu) = Cocc[nu*op + p]
+  RowsStrided acc{Cocc, 1, s->op, nullptr};
+  return slice_rows(acc, s->op, s->n, s->Kp, (long)s->op * s->Kp, s->Cdig, s->Cexp, st);
+}
+
+las_status split_half(SplitState* s, int l0, int nL, double* Ht, cudaStream_t st) {
+  const long rows = (long)nL * s->n;
+  const long plane = (long)s->X * s->n * s->Kp;
+  return ozaki_gemm(s->Bdig + (long)l0 * s->n * s->Kp, plane, s->Bexp + (long)l0 * s->n, rows,
+                    s->Cdig, (long)s->op * s->Kp, s->Cexp, s->op, s->n, s->Kp, 1, 1, Ht, 0, 0,
+                    s->n, s->op, s->status, st);
+}
+
+las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaStream_t st) {
+  const long R = (long)nL * s->op;
+  RowsStrided acc{Ht, s->n, 1, nullptr};
+  las_status rc = slice_rows(acc, R, s->n, s->Kp, (long)s->Lc * s->op * s->Kp, s->Hdig, s->Hexp,
+                             st);
+  if (rc != LAS_OK) return rc;
+  return ozaki_gemm(s->Hdig, (long)s->Lc * s->op * s->Kp, s->Hexp, R, s->Cdig,
+                    (long)s->op * s->Kp, s->Cexp, s->op, s->n, s->Kp, 1, 0, T, s->op, 0, 0, 0,
+                    s->status, st);
+}
+
+las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, int accumulate,
+                         cudaStream_t st) {
+  const long R = (long)nL * s->op;      // K of the projection: (L, p)
+  const long Rp = rup(R, 8);
+  las_status rc = transpose_planes(s->Hdig, R, s->n, s->Kp, (long)s->Lc * s->op * s->Kp,
+                                   s->HdigT, Rp, st);
+  if (rc != LAS_OK) return rc;
+  // W rows q (K = (L,p)), already scaled by 2^Hexp[(L,p)] and stored transposed: Wt[q][R]
+  RowsStrided acc{Wt, R, 1, nullptr};
+  rc = slice_rows(acc, s->op, R, Rp, (long)s->op * Rp, s->Wdig, s->Wexp, st);
+  if (rc != LAS_OK) return rc;
+  const int ks = (int)std::max(1L, std::min((long)s->ksplit6, (R + 32 * 64 - 1) / (32 * 64)));
+  rc = ozaki_gemm(s->HdigT, (long)s->n * Rp, nullptr, s->n, s->Wdig, (long)s->op * Rp, s->Wexp,
+                  s->op, R, Rp, ks, 0, s->part, s->op, (long)s->n * s->op, 0, 0, s->status, st);
+  if (rc != LAS_OK) return rc;
+  launch_reduce_partials(s->part, ks, (long)s->n * s->op, Out, accumulate, st);
+  return LAS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Standalone emulated-FP64 GEMM through the same kernels (C ABI)
+// ------------------------------------------------------------------------------------------
+static size_t sgemm_ws(long M, long N, long K) {
+  const long Kp = rup(K, 8);
+  return (size_t)NDIG * (M + N) * Kp * 2 + (size_t)(M + N) * 4 + 4096;
+}
+
+extern "C" size_t las_split_gemm_workspace(long M, long N, long K) {
+  if (M <= 0 || N <= 0 || K <= 0) return 0;
+  return sgemm_ws(M, N, K);
+}
+
+extern "C" las_status las_split_gemm(long M, long N, long K, const double* A, long lda,
+                                     const double* B, long ldb, double* C, long ldc,
+                                     void* workspace, size_t workspace_bytes, void* stream) {
+  if (M < 0 || N < 0 || K < 0) return LAS_ERR_ARG;
+  if (M == 0 || N == 0) return LAS_OK;
+  if (!A || !B || !C || !workspace) return LAS_ERR_ARG;
+  if (lda < K || ldb < N || ldc < N) return LAS_ERR_ARG;
+  if (workspace_bytes < sgemm_ws(M, N, K) || ((uintptr_t)workspace & 255)) return LAS_ERR_WORKSPACE;
+  if (K == 0) {
+    cudaStream_t st = (cudaStream_t)stream;
+    for (long r = 0; r < M; ++r)
+      LAS_CUDA_TRY(cudaMemsetAsync(C + r * ldc, 0, N * 8, st));
+    return LAS_OK;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const long Kp = rup(K, 8);
+  uint8_t* w = (uint8_t*)workspace;
+  __nv_bfloat16* Ad = (__nv_bfloat16*)w;
+  w += rup((long)NDIG * M * Kp * 2, 256);
+  __nv_bfloat16* Bd = (__nv_bfloat16*)w;
+  w += rup((long)NDIG * N * Kp * 2, 256);
+  int* ea = (int*)w;
+  w += rup(M * 4, 256);
+  int* eb = (int*)w;
+  w += rup(N * 4, 256);
+  int* status = (int*)w;
+  LAS_CUDA_TRY(cudaMemsetAsync(status, 0, 4, st));
+  las_status rc = slice_rows(RowsStrided{A, lda, 1, nullptr}, M, K, Kp, M * Kp, Ad, ea, st);
+  if (rc == LAS_OK)
+    rc = slice_rows(RowsStrided{B, 1, ldb, nullptr}, N, K, Kp, N * Kp, Bd, eb, st);
+  if (rc == LAS_OK)
+    rc = ozaki_gemm(Ad, M * Kp, ea, M, Bd, N * Kp, eb, N, K, Kp, 1, 0, C, ldc, 0, 0, 0, status, st);
+  if (rc != LAS_OK) return rc;
+  int h = 0;
+  LAS_CUDA_TRY(cudaMemcpyAsync(&h, status, 4, cudaMemcpyDeviceToHost, st));
+  LAS_CUDA_TRY(cudaStreamSynchronize(st));
+  return h ? (las_status)h : LAS_OK;
 }

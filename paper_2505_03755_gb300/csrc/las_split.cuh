@@ -4,11 +4,21 @@
 
 struct SplitState;
 
+// Builds the one-time digit planes of the packed Cholesky vectors.  Device errors (timeouts of
+// bounded waits) are recorded in *status.
 las_status split_create(SplitState** s, int n, int X, int op, int Lc, const double* Bp,
-                        cudaStream_t st, size_t* bytes);
+                        int* status, cudaStream_t st, size_t* bytes);
+// Device bytes per auxiliary index of the per-evaluation digit workspace.
+size_t split_bytes_per_aux(int n, int op);
+// Row exponents of the current chunk's half-transformed rows (L, p): the per-aux kernel scales
+// the projection matrix by 2^exp so that the exponents can be moved out of the left operand.
+const int* split_hexp(SplitState* s);
 void split_destroy(SplitState* s);
 las_status split_prepare_C(SplitState* s, const double* Cocc, cudaStream_t st);
-las_status split_half_full(SplitState* s, int l0, int nL, const double* Cocc, double* Ht,
-                           double* T, cudaStream_t st);
-las_status split_project(SplitState* s, int nL, const double* Ht, const double* W, double* Out,
-                         int accumulate, cudaStream_t st);
+// S1: Ht[b][p][mu] = sum_nu b^{l0+b}(mu,nu) C_occ(nu,p)   (b < nL)
+las_status split_half(SplitState* s, int l0, int nL, double* Ht, cudaStream_t st);
+// S2: T[b] = Ht[b] C_occ   (op x op per b)
+las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaStream_t st);
+// Out (+)= sum_{(L,p)} H(mu,(L,p)) W((L,p),q) with Wt[q][(L,p)] = W_L(p,q) * 2^exp(L,p)
+las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, int accumulate,
+                         cudaStream_t st);

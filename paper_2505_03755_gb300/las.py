@@ -20,7 +20,8 @@ PRECISIONS = {"fp64": LAS_FP64, "split": LAS_SPLIT_BF16, "split_bf16": LAS_SPLIT
 
 EXPORTS = ["las_create", "las_destroy", "las_set_stream", "las_sync", "las_device_bytes",
            "las_df_transform", "las_df_jk", "las_energy", "las_energy_grad",
-           "las_energy_grad_host", "las_set_timing", "las_stage_times", "las_status_str"]
+           "las_energy_grad_host", "las_set_timing", "las_stage_times", "las_kernel_launches",
+           "las_split_gemm_workspace", "las_split_gemm", "las_status_str"]
 
 
 class LasError(RuntimeError):
@@ -61,6 +62,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.las_set_timing.argtypes = [vp, i]
     lib.las_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
     lib.las_stage_times.restype = i
+    lib.las_split_gemm_workspace.argtypes = [ctypes.c_long] * 3
+    lib.las_split_gemm_workspace.restype = sz
+    lib.las_split_gemm.argtypes = [ctypes.c_long] * 3 + [vp, ctypes.c_long, vp, ctypes.c_long,
+                                                         vp, ctypes.c_long, vp, sz, vp]
+    lib.las_split_gemm.restype = i
+    lib.las_kernel_launches.argtypes = []
+    lib.las_kernel_launches.restype = ctypes.c_long
     lib.las_status_str.argtypes = [i]
     lib.las_status_str.restype = ctypes.c_char_p
     for name in ["las_create", "las_destroy", "las_set_stream", "las_sync", "las_df_transform",
@@ -69,6 +77,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         getattr(lib, name).restype = i
     _lib = lib
     return lib
+
+
+def kernel_launches() -> int:
+    """Kernels liblasdf has launched in this process so far."""
+    return int(load_library().las_kernel_launches())
 
 
 def _check(code: int, where: str) -> None:
@@ -197,6 +210,23 @@ class LasDF:
         _check(self._lib.las_df_transform(self._h, _ptr(C), p0, p1, _ptr(lmu), _ptr(lpu)),
                "las_df_transform")
         return lmu, lpu
+
+
+def split_gemm(A, B, out=None, stream=None):
+    """C = A @ B (float64 CUDA tensors) through the emulated-FP64 BF16 tensor-core GEMM."""
+    import torch
+    lib = load_library()
+    M, K = A.shape
+    K2, N = B.shape
+    if K2 != K:
+        raise ValueError("inner dimensions differ")
+    C = torch.empty((M, N), dtype=torch.float64, device=A.device) if out is None else out
+    nbytes = int(lib.las_split_gemm_workspace(M, N, K))
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=A.device)
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(lib.las_split_gemm(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C),
+                              C.stride(0), ws.data_ptr(), nbytes, st), "las_split_gemm")
+    return C
 
 
 def _energy_function():

@@ -34,8 +34,9 @@ def make_las(s, precision="fp64", **kw):
 
 def gpu_energy_grad(s, precision="fp64", want_gorb=True, **kw):
     las = make_las(s, precision, **kw)
-    E, G, g = las.energy_grad(dev(s.C), dev(s.h), dev(s.dm1s_flat()), dev(s.dm2_flat()),
-                              want_gorb=want_gorb)
+    res = las.energy_grad(dev(s.C), dev(s.h), dev(s.dm1s_flat()), dev(s.dm2_flat()),
+                          want_gorb=want_gorb)
+    E, G, g = res if want_gorb else (res[0], res[1], None)
     las.sync()
     out = float(E), G.cpu().numpy(), (g.cpu().numpy() if g is not None else None)
     las.close()

@@ -1,0 +1,113 @@
+"""Split-precision (BF16 digit, tcgen05) path: the emulated-FP64 GEMM and the full LAS chain."""
+import numpy as np
+import pytest
+
+from gpu_common import SMALL, built, dev, gpu_energy_grad, make_las, torch_cuda
+from las_inputs import config_system
+from oracle import las_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+E_ABS = 1e-8      # split mode: |dE| in Eh
+G_ABS = 1e-8      # split mode: max-abs on dE/dC
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch_cuda()
+    built()
+
+
+def _gemm(A, B):
+    from paper_2505_03755_gb300 import split_gemm
+    C = split_gemm(dev(A), dev(B))
+    return C.cpu().numpy()
+
+
+def test_split_gemm_integer_inputs_bit_exact():
+    rng = np.random.default_rng(1)
+    A = rng.integers(-100, 101, size=(300, 1000)).astype(np.float64)
+    B = rng.integers(-100, 101, size=(1000, 200)).astype(np.float64)
+    C = _gemm(A, B)
+    ref = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    assert np.array_equal(C, ref)
+
+
+def _digit_matrix(rows, cols, which, rng):
+    """Entries sum_s d_s 2^(-7-8s) over the digit positions `which` (|d_s| < 128); the first
+    column is 0.75 so that every row maximum lies in [0.5, 1)."""
+    a = np.zeros((rows, cols))
+    for s in which:
+        a += rng.integers(-127, 128, size=(rows, cols)).astype(np.float64) * 2.0 ** (-7 - 8 * s)
+    a[:, 0] = 0.75
+    return a
+
+
+@pytest.mark.parametrize("wa,wb", [([0], [0]), ([1], [0]), ([0], [1]), ([1], [1]), ([2], [0]),
+                                   ([0, 1], [0, 1]), ([3], [0]), ([0], [3]), ([1], [2]),
+                                   ([0, 1, 2], [0, 1]), ([4], [0])])
+def test_split_gemm_digit_groups_bit_exact(wa, wb):
+    """Operands made of chosen BF16 digits: every kept digit product is formed exactly (the four
+    leading weight groups accumulate exactly; a single tail weight is exact in FP32), so the
+    result equals the exact product bit for bit.  (Weight 2^-40 alone is not tested this way: an
+    exact result with terms 2^-54 below its leading term is not representable in FP64.)"""
+    rng = np.random.default_rng(len(wa) * 10 + sum(wa) + 7 * sum(wb))
+    A = _digit_matrix(128, 352, wa, rng)
+    B = np.ascontiguousarray(_digit_matrix(96, 352, wb, rng).T)
+    assert np.array_equal(_gemm(A, B), A @ B)
+
+
+@pytest.mark.parametrize("M,K,N", [(1, 5, 3), (128, 32, 96), (257, 1111, 190), (130, 700, 16)])
+def test_split_gemm_random_fp64(M, K, N):
+    rng = np.random.default_rng(M + K + N)
+    A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-3, 3, size=(M, 1)))
+    B = rng.standard_normal((K, N)) * np.exp(rng.uniform(-3, 3, size=(1, N)))
+    C = _gemm(A, B)
+    ref = A @ B
+    # error budget per product term, relative to row max x column max: operand rounding
+    # (2 x 2^-48), dropped digit pairs of weight 2^-48 (5 x 2^-48) and the FP32 tail of weights
+    # 2^-32 and 2^-40 (11 x 2^-56), i.e. below 2^-43 * K * rowmax * colmax
+    rm = np.abs(A).max(axis=1)[:, None]
+    cm = np.abs(B).max(axis=0)[None, :]
+    err = np.abs(C - ref)
+    assert np.all(err <= 2.0 ** -43 * K * rm * cm), (err / (K * rm * cm)).max()
+    # and the typical error (random signs) grows like sqrt(K), well below the worst case
+    assert np.sqrt(np.mean((err / (rm * cm)) ** 2)) <= 2.0 ** -44 * np.sqrt(K)
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_energy_grad_small_split(name):
+    s = SMALL[name]()
+    ref = O.system_energy_grad(s)
+    E, G, g = gpu_energy_grad(s, "split")
+    assert abs(E - ref["E"]) <= E_ABS, (E, ref["E"])
+    assert np.abs(G - ref["G"]).max() <= G_ABS
+    assert np.abs(g - ref["gorb"]).max() <= 10 * G_ABS
+
+
+def test_split_chunked_workspace_same_result():
+    s = SMALL["ragged"]()
+    E0, G0, _ = gpu_energy_grad(s, "split")
+    E1, G1, _ = gpu_energy_grad(s, "split", max_workspace_bytes=2_000_000)
+    assert abs(E1 - E0) <= 1e-10
+    assert np.abs(G1 - G0).max() <= 1e-10
+
+
+def test_split_autograd():
+    from paper_2505_03755_gb300 import las_energy
+    s = SMALL["cfg0"]()
+    las = make_las(s, "split")
+    C = dev(s.C).requires_grad_(True)
+    E = las_energy(C, las, dev(s.h), dev(s.dm1s_flat()), dev(s.dm2_flat()))
+    E.backward()
+    ref = O.system_energy_grad(s)
+    assert np.abs(C.grad.cpu().numpy() - ref["G"]).max() <= G_ABS
+    las.close()
+
+
+def test_config1_split():
+    s = config_system(1)
+    ref = O.system_energy_grad(s)
+    E, G, _ = gpu_energy_grad(s, "split", want_gorb=False)
+    assert abs(E - ref["E"]) <= E_ABS
+    assert np.abs(G - ref["G"]).max() <= G_ABS
