@@ -166,7 +166,7 @@ extern "C" las_status las_create(las_ctx** out, const las_dims* d, const double*
   // Workspace plan: the largest auxiliary chunk that fits the cap.
   const size_t fixed = sizeof(double) * ((size_t)x->n * x->op * 4 + (size_t)x->op * x->op +
                                          (size_t)x->nmo * x->op + 3 * (size_t)x->X + x->npair);
-  size_t cap = max_ws ? max_ws : (size_t)24 << 30;
+  size_t cap = max_ws ? max_ws : (size_t)64 << 30;
   int Lc = x->X;
   while (Lc > 1 && fixed + chunk_bytes(x, Lc) + (size_t)64 * x->n * x->op * 8 > cap) Lc = (Lc + 1) / 2;
   if (fixed + chunk_bytes(x, Lc) > cap) {
@@ -362,7 +362,9 @@ static las_status evaluate(las_ctx* x, const double* C, const double* h, const d
     if (with_grad && (st = project(x, nL, l0 > 0)) != LAS_OK) return st;
     if (l0 == 0) stage_mark(x, 4);
   }
-  {  // one-electron pieces: hC = h C_occ, hmo = C_occ^T hC
+  if (x->prec == LAS_SPLIT_BF16) {  // one-electron pieces: hC = h C_occ, hmo = C_occ^T hC
+    if ((st = split_one_electron(x->split, h, x->hC, x->hmo, x->stream)) != LAS_OK) return st;
+  } else {
     StridedA Ah{h, 0, n, 1};
     StridedA Bc{x->Cocc, 0, op, 1};
     StridedC Ch{x->hC, 0, op, 1, 1.0, 0};

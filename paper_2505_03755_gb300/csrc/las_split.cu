@@ -300,8 +300,44 @@ struct RowsPacked {   // element (r = L*n + mu, k = nu) of the packed symmetric 
   }
 };
 
-// One warp per row r < R: exponent e_r with max|x| < 2^e_r, digit planes
-// planes[s][r][k] = bf16(d_s * 2^-8s) for k < K and 0 for K <= k < Kp.
+// Six balanced base-256 digits of x * 2^-e rounded at 2^-47 (|x| < 2^e), returned as the BF16
+// plane values d_s * 2^-8s.  Integer operations on the bit pattern only.
+__device__ __forceinline__ void digits_of(double xv, int e, __nv_bfloat16 (&out)[NDIG]) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(xv);
+  const int bex = (int)((b >> 52) & 0x7FF);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  int ee = bex;
+  if (bex != 0) m |= (1ull << 52); else ee = 1;
+  // |x| * 2^(47 - e) = m * 2^(ee - 1075 + 47 - e)
+  const int shift = ee - 1028 - e;
+  unsigned long long y;
+  if (shift >= 0) y = m << shift;
+  else if (shift > -63) y = (m + (1ull << (-shift - 1))) >> (-shift);
+  else y = 0;
+  long long Y = (b >> 63) ? -(long long)y : (long long)y;
+  int d[NDIG];
+#pragma unroll
+  for (int s = NDIG - 1; s >= 1; --s) {
+    const long long t = ((Y + 128) & 255) - 128;
+    d[s] = (int)t;
+    Y = (Y - t) >> 8;
+  }
+  d[0] = (int)Y;
+#pragma unroll
+  for (int s = 0; s < NDIG; ++s)
+    out[s] = __float2bfloat16_rn((float)d[s] * __int_as_float((127 - 8 * s) << 23));
+}
+
+__device__ __forceinline__ int exp_of_maxbits(unsigned long long mx) {
+  return mx ? (int)((mx >> 52) & 0x7FF) - 1022 : 0;   // max|x| < 2^e
+}
+
+__device__ __forceinline__ unsigned long long absbits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Short rows: one warp per row r < R; exponent e_r with max|x| < 2^e_r and digit planes
+// planes[s*plane + r*Kp + k] for k < K (zero for K <= k < Kp).
 template <class Acc>
 __global__ void __launch_bounds__(256)
 k_slice_rows(Acc acc, long R, long K, long Kp, long plane, __nv_bfloat16* planes, int* ex) {
@@ -310,64 +346,118 @@ k_slice_rows(Acc acc, long R, long K, long Kp, long plane, __nv_bfloat16* planes
   if (r >= R) return;
   unsigned long long mx = 0;
   for (long k = lane; k < K; k += 32) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(acc(r, k)) & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long b = absbits(acc(r, k));
     mx = b > mx ? b : mx;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
     mx = v > mx ? v : mx;
   }
-  const int e = mx ? (int)((mx >> 52) & 0x7FF) - 1022 : 0;   // max|x| < 2^e
+  const int e = exp_of_maxbits(mx);
   if (lane == 0) ex[r] = e;
   for (long k = lane; k < Kp; k += 32) {
-    long long Y = 0;
-    if (k < K) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(acc(r, k));
-      const int bex = (int)((b >> 52) & 0x7FF);
-      unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-      int ee = bex;
-      if (bex != 0) m |= (1ull << 52); else ee = 1;
-      // |x| * 2^(47 - e) = m * 2^(ee - 1075 + 47 - e)
-      const int shift = ee - 1028 - e;
-      unsigned long long y;
-      if (shift >= 0) y = m << shift;
-      else if (shift > -63) y = (m + (1ull << (-shift - 1))) >> (-shift);
-      else y = 0;
-      Y = (b >> 63) ? -(long long)y : (long long)y;
-    }
-    int d[NDIG];
+    __nv_bfloat16 d[NDIG];
+    digits_of(k < K ? acc(r, k) : 0.0, e, d);
 #pragma unroll
-    for (int s = NDIG - 1; s >= 1; --s) {
-      const long long t = ((Y + 128) & 255) - 128;
-      d[s] = (int)t;
-      Y = (Y - t) >> 8;
-    }
-    d[0] = (int)Y;
-#pragma unroll
-    for (int s = 0; s < NDIG; ++s) {
-      const float f = (float)d[s] * __int_as_float((127 - 8 * s) << 23);
-      planes[s * plane + r * Kp + k] = __float2bfloat16_rn(f);
-    }
+    for (int s = 0; s < NDIG; ++s) planes[s * plane + r * Kp + k] = d[s];
   }
 }
 
-// planes [NDIG][R][Kin] -> out [NDIG][Kin][Rout] (transpose of every plane; rows >= R are 0)
-__global__ void k_transpose_planes(const __nv_bfloat16* in, long R, long Kin, long Kp_in,
-                                   long in_plane, __nv_bfloat16* out, long Rp_out) {
-  __shared__ __nv_bfloat16 tile[32][33];
-  const int s = blockIdx.z;
-  const long r0 = (long)blockIdx.y * 32, k0 = (long)blockIdx.x * 32;
-  const __nv_bfloat16* src = in + (long)s * in_plane;
-  __nv_bfloat16* dst = out + (long)s * Kin * Rp_out;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const long r = r0 + i, k = k0 + threadIdx.x;
-    tile[i][threadIdx.x] = (r < R && k < Kin) ? src[r * Kp_in + k] : __float2bfloat16_rn(0.f);
+// Long rows, pass 1: mx[r] = max_k |x(r,k)| as ordered bit patterns (grid: segments x rows).
+template <class Acc>
+__global__ void __launch_bounds__(256)
+k_rowmax_long(Acc acc, long K, long seg, unsigned long long* mx) {
+  __shared__ unsigned long long red[8];
+  const long r = blockIdx.y;
+  const long k0 = (long)blockIdx.x * seg, k1 = min(K, k0 + seg);
+  unsigned long long m = 0;
+  for (long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    const unsigned long long b = absbits(acc(r, k));
+    m = b > m ? b : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
+    if (m) atomicMax(&mx[r], m);
+  }
+}
+
+// Long rows, pass 2: element-parallel digits (grid covers R x Kp).
+template <class Acc>
+__global__ void __launch_bounds__(256)
+k_digits_long(Acc acc, long R, long K, long Kp, long plane, const unsigned long long* mx,
+              __nv_bfloat16* planes, int* ex) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= R * Kp) return;
+  const long r = i / Kp, k = i - r * Kp;
+  const int e = exp_of_maxbits(mx[r]);
+  if (k == 0) ex[r] = e;
+  __nv_bfloat16 d[NDIG];
+  digits_of(k < K ? acc(r, k) : 0.0, e, d);
+#pragma unroll
+  for (int s = 0; s < NDIG; ++s) planes[s * plane + r * Kp + k] = d[s];
+}
+
+// Half-transformed rows (L,p) of Ht [R][n]: exponents, row-major digit planes
+// Hd[s][r][k] (k < Kp) and transposed planes HdT[s][k][r] (k < n, r < Rp), in one pass.
+// Block: 32 consecutive rows, 8 warps.
+__global__ void __launch_bounds__(256)
+k_slice_ht(const double* __restrict__ Ht, long R, int n, long Kp, long plane,
+           __nv_bfloat16* __restrict__ Hd, long Rp, long planeT, __nv_bfloat16* __restrict__ HdT,
+           int* __restrict__ ex) {
+  __shared__ __nv_bfloat16 tile[NDIG][32][34];
+  __shared__ int es[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long r0 = (long)blockIdx.x * 32;
+  for (int i = 0; i < 4; ++i) {
+    const int row = warp * 4 + i;
+    const long r = r0 + row;
+    unsigned long long mx = 0;
+    if (r < R)
+      for (int k = lane; k < n; k += 32) {
+        const unsigned long long b = absbits(Ht[r * n + k]);
+        mx = b > mx ? b : mx;
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = v > mx ? v : mx;
+    }
+    if (lane == 0) {
+      es[row] = exp_of_maxbits(mx);
+      if (r < R) ex[r] = es[row];
+    }
   }
   __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const long k = k0 + i, r = r0 + threadIdx.x;
-    if (k < Kin && r < Rp_out) dst[k * Rp_out + r] = tile[threadIdx.x][i];
+  for (long k0 = 0; k0 < Kp; k0 += 32) {
+    for (int i = 0; i < 4; ++i) {
+      const int row = warp + 8 * i;
+      const long r = r0 + row, k = k0 + lane;
+      __nv_bfloat16 d[NDIG];
+      digits_of((r < R && k < n) ? Ht[r * n + k] : 0.0, es[row], d);
+#pragma unroll
+      for (int s = 0; s < NDIG; ++s) {
+        tile[s][row][lane] = d[s];
+        if (r < R && k < Kp) Hd[s * plane + r * Kp + k] = d[s];
+      }
+    }
+    __syncthreads();
+    for (int i = 0; i < 4; ++i) {
+      const int kk = warp * 4 + i;
+      const long k = k0 + kk, r = r0 + lane;
+      if (k < n && r < Rp) {
+#pragma unroll
+        for (int s = 0; s < NDIG; ++s) HdT[s * planeT + k * Rp + r] = tile[s][lane][kk];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -475,29 +565,32 @@ las_status ozaki_gemm(const __nv_bfloat16* Ad, long a_plane, const int* ea, long
 
 template <class Acc>
 static las_status slice_rows(Acc acc, long R, long K, long Kp, long plane, __nv_bfloat16* planes,
-                             int* ex, cudaStream_t st) {
+                             int* ex, cudaStream_t st, unsigned long long* mx_ws = nullptr) {
   if (R <= 0) return LAS_OK;
-  const long threads = R * 32;
-  k_slice_rows<Acc><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(acc, R, K, Kp, plane,
-                                                                        planes, ex);
-  las_count_launch();
+  if (K > 8192 && mx_ws && R <= 65535) {
+    // long rows: block-parallel maxima, then element-parallel digits
+    cudaError_t e0 = cudaMemsetAsync(mx_ws, 0, R * sizeof(unsigned long long), st);
+    if (e0 != cudaSuccess) {
+      las_record_cuda_error(e0, "cudaMemsetAsync(rowmax)", __FILE__, __LINE__);
+      return LAS_ERR_CUDA;
+    }
+    const long seg = 8192;
+    dim3 g1((unsigned)((K + seg - 1) / seg), (unsigned)R);
+    k_rowmax_long<Acc><<<g1, 256, 0, st>>>(acc, K, seg, mx_ws);
+    las_count_launch();
+    const long tot = R * Kp;
+    k_digits_long<Acc><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(acc, R, K, Kp, plane,
+                                                                      mx_ws, planes, ex);
+    las_count_launch();
+  } else {
+    const long threads = R * 32;
+    k_slice_rows<Acc><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(acc, R, K, Kp, plane,
+                                                                          planes, ex);
+    las_count_launch();
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     las_record_cuda_error(e, "k_slice_rows launch", __FILE__, __LINE__);
-    return LAS_ERR_CUDA;
-  }
-  return LAS_OK;
-}
-
-static las_status transpose_planes(const __nv_bfloat16* in, long R, long Kin, long Kp_in,
-                                   long in_plane, __nv_bfloat16* out, long Rp_out,
-                                   cudaStream_t st) {
-  dim3 grid((unsigned)((Kin + 31) / 32), (unsigned)((Rp_out + 31) / 32), NDIG);
-  k_transpose_planes<<<grid, dim3(32, 8), 0, st>>>(in, R, Kin, Kp_in, in_plane, out, Rp_out);
-  las_count_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    las_record_cuda_error(e, "k_transpose_planes launch", __FILE__, __LINE__);
     return LAS_ERR_CUDA;
   }
   return LAS_OK;
@@ -517,13 +610,18 @@ struct SplitState {
   __nv_bfloat16* Wdig;   // [NDIG][op][Rp]
   int* Wexp;             // [op]
   double* part;          // [ksplit][n][op]
+  unsigned long long* mx;  // [op] row maxima for long-row slicing
+  __nv_bfloat16* hdig;   // [NDIG][n][Kp]   one-electron h
+  int* hexp;             // [n]
+  __nv_bfloat16* hcdig;  // [NDIG][op][Kp]  columns of h C_occ
+  int* hcexp;            // [op]
   int ksplit6;
   int* status;
 };
 
 static void split_free(SplitState* s) {
   void* ptrs[] = {s->Bdig, s->Bexp, s->Cdig, s->Cexp, s->Hdig, s->Hexp, s->HdigT, s->Wdig,
-                  s->Wexp, s->part};
+                  s->Wexp, s->part, s->mx, s->hdig, s->hexp, s->hcdig, s->hcexp};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -573,6 +671,11 @@ las_status split_create(SplitState** out, int n, int X, int op, int Lc, const do
   A((void**)&s->Wdig, (size_t)NDIG * op * s->Rp * 2);
   A((void**)&s->Wexp, (size_t)op * 4);
   A((void**)&s->part, (size_t)s->ksplit6 * n * op * 8);
+  A((void**)&s->mx, (size_t)op * 8);
+  A((void**)&s->hdig, (size_t)NDIG * n * s->Kp * 2);
+  A((void**)&s->hexp, (size_t)n * 4);
+  A((void**)&s->hcdig, (size_t)NDIG * op * s->Kp * 2);
+  A((void**)&s->hcexp, (size_t)op * 4);
   if (rc == LAS_OK) {
     // one-time digit planes of the Cholesky vectors: rows (L, mu), K = nu
     RowsPacked acc{Bp, (long)n * (n + 1) / 2, n};
@@ -612,10 +715,18 @@ las_status split_half(SplitState* s, int l0, int nL, double* Ht, cudaStream_t st
 
 las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaStream_t st) {
   const long R = (long)nL * s->op;
-  RowsStrided acc{Ht, s->n, 1, nullptr};
-  las_status rc = slice_rows(acc, R, s->n, s->Kp, (long)s->Lc * s->op * s->Kp, s->Hdig, s->Hexp,
-                             st);
-  if (rc != LAS_OK) return rc;
+  const long Rp = rup(R, 8);
+  k_slice_ht<<<(unsigned)((Rp + 31) / 32), 256, 0, st>>>(Ht, R, s->n, s->Kp,
+                                                         (long)s->Lc * s->op * s->Kp, s->Hdig, Rp,
+                                                         (long)s->n * Rp, s->HdigT, s->Hexp);
+  las_count_launch();
+  {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      las_record_cuda_error(e, "k_slice_ht launch", __FILE__, __LINE__);
+      return LAS_ERR_CUDA;
+    }
+  }
   return ozaki_gemm(s->Hdig, (long)s->Lc * s->op * s->Kp, s->Hexp, R, s->Cdig,
                     (long)s->op * s->Kp, s->Cexp, s->op, s->n, s->Kp, 1, 0, T, s->op, 0, 0, 0,
                     s->status, st);
@@ -625,12 +736,10 @@ las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, i
                          cudaStream_t st) {
   const long R = (long)nL * s->op;      // K of the projection: (L, p)
   const long Rp = rup(R, 8);
-  las_status rc = transpose_planes(s->Hdig, R, s->n, s->Kp, (long)s->Lc * s->op * s->Kp,
-                                   s->HdigT, Rp, st);
-  if (rc != LAS_OK) return rc;
+  // the transposed digit planes of H (HdigT) were written by split_full
   // W rows q (K = (L,p)), already scaled by 2^Hexp[(L,p)] and stored transposed: Wt[q][R]
   RowsStrided acc{Wt, R, 1, nullptr};
-  rc = slice_rows(acc, s->op, R, Rp, (long)s->op * Rp, s->Wdig, s->Wexp, st);
+  las_status rc = slice_rows(acc, s->op, R, Rp, (long)s->op * Rp, s->Wdig, s->Wexp, st, s->mx);
   if (rc != LAS_OK) return rc;
   const int ks = (int)std::max(1L, std::min((long)s->ksplit6, (R + 32 * 64 - 1) / (32 * 64)));
   rc = ozaki_gemm(s->HdigT, (long)s->n * Rp, nullptr, s->n, s->Wdig, (long)s->op * Rp, s->Wexp,
@@ -638,6 +747,24 @@ las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, i
   if (rc != LAS_OK) return rc;
   launch_reduce_partials(s->part, ks, (long)s->n * s->op, Out, accumulate, st);
   return LAS_OK;
+}
+
+las_status split_one_electron(SplitState* s, const double* h, double* hC, double* hmo,
+                              cudaStream_t st) {
+  // hC = h C_occ  (rows mu of h, columns p of C_occ: the digits of C_occ are already sliced)
+  las_status rc = slice_rows(RowsStrided{h, s->n, 1, nullptr}, s->n, s->n, s->Kp,
+                             (long)s->n * s->Kp, s->hdig, s->hexp, st);
+  if (rc == LAS_OK)
+    rc = ozaki_gemm(s->hdig, (long)s->n * s->Kp, s->hexp, s->n, s->Cdig, (long)s->op * s->Kp,
+                    s->Cexp, s->op, s->n, s->Kp, 1, 0, hC, s->op, 0, 0, 0, s->status, st);
+  // hmo = C_occ^T hC  (rows p of C_occ^T are the C_occ digit rows; columns q of hC)
+  if (rc == LAS_OK)
+    rc = slice_rows(RowsStrided{hC, 1, s->op, nullptr}, s->op, s->n, s->Kp, (long)s->op * s->Kp,
+                    s->hcdig, s->hcexp, st);
+  if (rc == LAS_OK)
+    rc = ozaki_gemm(s->Cdig, (long)s->op * s->Kp, s->Cexp, s->op, s->hcdig, (long)s->op * s->Kp,
+                    s->hcexp, s->op, s->n, s->Kp, 1, 0, hmo, s->op, 0, 0, 0, s->status, st);
+  return rc;
 }
 
 // ------------------------------------------------------------------------------------------

@@ -19,6 +19,9 @@ las_status split_prepare_C(SplitState* s, const double* Cocc, cudaStream_t st);
 las_status split_half(SplitState* s, int l0, int nL, double* Ht, cudaStream_t st);
 // S2: T[b] = Ht[b] C_occ   (op x op per b)
 las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaStream_t st);
+// hC = h C_occ and hmo = C_occ^T hC (split_prepare_C must have run for this C)
+las_status split_one_electron(SplitState* s, const double* h, double* hC, double* hmo,
+                              cudaStream_t st);
 // Out (+)= sum_{(L,p)} H(mu,(L,p)) W((L,p),q) with Wt[q][(L,p)] = W_L(p,q) * 2^exp(L,p)
 las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, int accumulate,
                          cudaStream_t st);
