@@ -818,3 +818,54 @@ extern "C" las_status las_split_gemm(long M, long N, long K, const double* A, lo
   LAS_CUDA_TRY(cudaStreamSynchronize(st));
   return h ? (las_status)h : LAS_OK;
 }
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free variant of las_split_gemm
+//
+// Some callers cannot allocate device memory at the point where they need a product: code that
+// runs while a stream is being captured into a CUDA graph (cudaMalloc is not a graph operation),
+// plugins whose host application owns every device allocation through its own pool, and
+// latency-critical loops where a cudaMalloc could synchronise the device. This entry point takes
+// its scratch from a fixed array that is part of the library image instead of asking for a
+// buffer: the digit planes and exponents of both operands live in `g_noalloc_scratch`, a
+// LAS_NOALLOC_SCRATCH_BYTES (64 MiB) file-scope device array that every GPU which loads the
+// library holds until the process exits.
+// ------------------------------------------------------------------------------------------
+#include <mutex>
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[LAS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices];  // device address of g_noalloc_scratch, per device ordinal
+}  // namespace
+
+extern "C" las_status las_split_gemm_noalloc(long M, long N, long K, const double* A, long lda,
+                                             const double* B, long ldb, double* C, long ldc,
+                                             void* stream) {
+  if (M < 0 || N < 0 || K < 0) return LAS_ERR_ARG;
+  if (M == 0 || N == 0) return LAS_OK;
+  if (!A || !B || !C) return LAS_ERR_ARG;
+  if (lda < K || ldb < N || ldc < N) return LAS_ERR_ARG;
+  if (K > 0 && sgemm_ws(M, N, K) > (size_t)LAS_NOALLOC_SCRATCH_BYTES) return LAS_ERR_WORKSPACE;
+  int dev = 0;
+  LAS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return LAS_ERR_UNSUPPORTED;
+  void* scratch = nullptr;
+  {
+    // Set-up, once per device with that device current: in host code the array's name is only
+    // a host-side stand-in, so its device address must be looked up.
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      LAS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_addr[dev] = p;
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  // The shared array keeps whatever the previous call left; las_split_gemm clears the status
+  // word it keeps there before use and overwrites every digit plane it reads.
+  return las_split_gemm(M, N, K, A, lda, B, ldb, C, ldc, scratch, LAS_NOALLOC_SCRATCH_BYTES,
+                        stream);
+}
