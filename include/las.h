@@ -121,12 +121,13 @@ las_status las_energy_grad_host(las_ctx* ctx, const double* C_host, const double
                                 const double* dm1s_host, const double* dm2_host,
                                 double* E_host, double* dEdC_host);
 
-/* Per-stage device times (milliseconds) of the last evaluation when timing is enabled with
- * las_set_timing(ctx, 1), measured with CUDA events on the context's stream.  Stage order:
- * [0] C packing and half transform (S1), [1] occupied full transform (S2), [2] per-aux
- * contractions, [3] projections (S5/S6), [4] one-electron terms, energy and gradient assembly.
- * With more than one auxiliary chunk, stages 0-3 cover the first chunk only.
- * Returns the number of stages written (<= cap). */
+/* Per-stage device times (milliseconds), averaged over the evaluations run since timing was
+ * enabled with las_set_timing(ctx, 1) or since the last las_stage_times call (up to the last
+ * 64), measured with CUDA events recorded on the context's stream inside each evaluation; only
+ * the last evaluation's final event is waited for.  Stage order: [0] C packing and half
+ * transform (S1), [1] occupied full transform (S2), [2] per-aux contractions, [3] projections
+ * (S5/S6), [4] one-electron terms, energy and gradient assembly.  With more than one auxiliary
+ * chunk, stages 0-3 cover the first chunk only.  Returns the number of stages written (<= cap). */
 las_status las_set_timing(las_ctx* ctx, int enable);
 int las_stage_times(las_ctx* ctx, float* ms, int cap);
 

@@ -20,6 +20,9 @@
 #include "las_common.cuh"
 #include "las_split.cuh"
 
+#define LAS_TIMING_RING 64
+#define LAS_MARKS 6
+
 #include <atomic>
 
 static thread_local char g_last_error[512];
@@ -66,10 +69,10 @@ struct las_ctx {
   size_t bytes;
   // split-precision state (owned)
   SplitState* split;
-  // timing
+  // timing: a ring of LAS_TIMING_RING evaluations x 6 stage marks, read without per-call syncs
   int timing;
-  cudaEvent_t ev[8];
-  float stage_ms[8];
+  cudaEvent_t* ev;       // [LAS_TIMING_RING][6]
+  int slot, recorded;
   int nstage;
 };
 
@@ -105,8 +108,11 @@ static void free_all(las_ctx* x) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (x->split) split_destroy(x->split);
-  for (int i = 0; i < 8; ++i)
-    if (x->ev[i]) cudaEventDestroy(x->ev[i]);
+  if (x->ev) {
+    for (int i = 0; i < LAS_TIMING_RING * LAS_MARKS; ++i)
+      if (x->ev[i]) cudaEventDestroy(x->ev[i]);
+    free(x->ev);
+  }
 }
 
 static size_t chunk_bytes(const las_ctx* x, int Lc) {
@@ -271,28 +277,48 @@ extern "C" las_status las_sync(las_ctx* x) {
 
 extern "C" las_status las_set_timing(las_ctx* x, int enable) {
   if (!x) return LAS_ERR_ARG;
-  if (enable && !x->ev[0])
-    for (int i = 0; i < 8; ++i) LAS_CUDA_TRY(cudaEventCreate(&x->ev[i]));
+  if (enable && !x->ev) {
+    x->ev = (cudaEvent_t*)calloc(LAS_TIMING_RING * LAS_MARKS, sizeof(cudaEvent_t));
+    if (!x->ev) return LAS_ERR_INTERNAL;
+    for (int i = 0; i < LAS_TIMING_RING * LAS_MARKS; ++i)
+      LAS_CUDA_TRY(cudaEventCreate(&x->ev[i]));
+  }
   x->timing = enable;
+  x->slot = 0;
+  x->recorded = 0;
   return LAS_OK;
 }
 
+// Average per-stage time over the evaluations recorded since timing was enabled or last read
+// (at most LAS_TIMING_RING of them); waits for the last one only.
 extern "C" int las_stage_times(las_ctx* x, float* ms, int cap) {
-  if (!x || !x->timing || x->nstage == 0) return 0;
-  if (cudaEventSynchronize(x->ev[x->nstage]) != cudaSuccess) return 0;
+  if (!x || !x->timing || x->recorded == 0 || x->nstage == 0) return 0;
+  const int nrec = x->recorded < LAS_TIMING_RING ? x->recorded : LAS_TIMING_RING;
+  const int last = (x->slot + LAS_TIMING_RING - 1) % LAS_TIMING_RING;
+  if (cudaEventSynchronize(x->ev[last * LAS_MARKS + x->nstage]) != cudaSuccess) return 0;
   int k = 0;
   for (; k < x->nstage && k < cap; ++k) {
-    float t = 0.f;
-    cudaEventElapsedTime(&t, x->ev[k], x->ev[k + 1]);
-    ms[k] = t;
+    double acc = 0.0;
+    for (int r = 0; r < nrec; ++r) {
+      const int sl = (x->slot + LAS_TIMING_RING - 1 - r) % LAS_TIMING_RING;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, x->ev[sl * LAS_MARKS + k], x->ev[sl * LAS_MARKS + k + 1]);
+      acc += t;
+    }
+    ms[k] = (float)(acc / nrec);
   }
+  x->recorded = 0;
   return k;
 }
 
 static inline void stage_mark(las_ctx* x, int i) {
-  if (x->timing && i < 8) {
-    cudaEventRecord(x->ev[i], x->stream);
+  if (x->timing && i < LAS_MARKS) {
+    cudaEventRecord(x->ev[x->slot * LAS_MARKS + i], x->stream);
     if (i > 0) x->nstage = i;
+    if (i == LAS_MARKS - 1) {
+      x->slot = (x->slot + 1) % LAS_TIMING_RING;
+      ++x->recorded;
+    }
   }
 }
 

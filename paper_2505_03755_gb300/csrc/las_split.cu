@@ -30,15 +30,15 @@ namespace lasdf_split {
 constexpr int NDIG = 6;
 constexpr int BM = 128;          // rows per CTA tile (tcgen05 M)
 constexpr int BN = 96;           // columns per CTA tile (tcgen05 N)
-constexpr int BK = 32;           // K per pipeline stage (one 64-byte swizzle row of BF16)
-constexpr int NSTAGE = 2;
+constexpr int BK = 16;           // K per pipeline stage (one 32-byte swizzle row of BF16)
+constexpr int NSTAGE = 5;
 constexpr int NEXACT = 4;        // exact weight groups q = 0..3
-constexpr int CHUNK = 8;         // stages per exact chunk (256 values of k)
-constexpr int A_PLANE = BM * BK * 2;                 // 8192 B
-constexpr int B_PLANE = BN * BK * 2;                 // 6144 B
-constexpr int A_BYTES = NDIG * A_PLANE;              // 49152
-constexpr int B_BYTES = NDIG * B_PLANE;              // 36864
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;       // 86016
+constexpr int CHUNK = 16;        // stages per exact chunk (256 values of k)
+constexpr int A_PLANE = BM * BK * 2;                 // 4096 B
+constexpr int B_PLANE = BN * BK * 2;                 // 3072 B
+constexpr int A_BYTES = NDIG * A_PLANE;              // 24576
+constexpr int B_BYTES = NDIG * B_PLANE;              // 18432
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;       // 43008 (42 KiB)
 constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256;
 constexpr int TMEM_COLS = 512;
 constexpr int COL_EXACT0 = 0;    // exact groups q = 0..3 at 0, 96, 192, 288; tail at 384
@@ -46,10 +46,42 @@ constexpr int COL_TAIL = NEXACT * BN;
 constexpr int NTHREADS = 320;    // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 constexpr uint32_t IDESC = sm100::idesc_bf16(BM, BN);
 
+// Digit planes are stored K-blocked: element (s, r, k) of an operand with R rows lives at
+//   s*plane + (k / BK) * (Rpad * BK) + r * BK + (k % BK),   Rpad = R rounded up to ROWPAD,
+// so that every pipeline stage of every tile is one contiguous block per plane.
+constexpr long ROWPAD = 384;     // common multiple of the two tile heights (128, 96)
+
+struct Planes {
+  __nv_bfloat16* p;
+  long R, Rpad, K, nkb, plane;   // rows, padded rows, K, K blocks, elements per plane
+  __host__ __device__ __forceinline__ long idx(int s, long r, long k) const {
+    return s * plane + (k / BK) * (Rpad * BK) + r * BK + (k % BK);
+  }
+};
+
+static inline long planes_rpad(long R) { return (R + ROWPAD - 1) / ROWPAD * ROWPAD; }
+static inline long planes_nkb(long K) { return (K + BK - 1) / BK; }
+static inline size_t planes_bytes(long R, long K) {
+  return (size_t)NDIG * planes_rpad(R) * planes_nkb(K) * BK * 2;
+}
+static inline Planes make_planes(void* p, long R, long K) {
+  Planes P;
+  P.p = (__nv_bfloat16*)p;
+  P.R = R;
+  P.Rpad = planes_rpad(R);
+  P.K = K;
+  P.nkb = planes_nkb(K);
+  P.plane = P.nkb * P.Rpad * BK;
+  return P;
+}
+
 struct OzParams {
   int M, N;                // output rows / columns
+  int a_rpad, b_rpad;      // padded rows of the A / B plane layouts
+  int a_row0, b_row0;      // first row of A / B used (row offset inside the layouts)
   int kb_total;            // K blocks of BK
   int kb_per_split;
+  int ksplit;
   const int* ea;           // row exponents [M] (nullptr: 0)
   const int* eb;           // column exponents [N]
   double* out;
@@ -85,6 +117,25 @@ __device__ __forceinline__ double make_double(long long W, int E) {
   return __longlong_as_double((long long)bits);
 }
 
+__device__ __forceinline__ void tile_coords(const OzParams& p, long t, int& m0, int& n0,
+                                            int& kb0, int& nkb) {
+  const int ntn = (p.N + BN - 1) / BN, ntm = (p.M + BM - 1) / BM;
+  const long per_z = (long)ntn * ntm;
+  const int z = (int)(t / per_z);
+  const long rem = t - (long)z * per_z;
+  // the column tiles of one row tile are adjacent in tile order so that concurrently running
+  // CTAs share that row tile's digit planes through L2
+  m0 = (int)(rem / ntn) * BM;
+  n0 = (int)(rem % ntn) * BN;
+  kb0 = z * p.kb_per_split;
+  nkb = min(p.kb_total, kb0 + p.kb_per_split) - kb0;
+}
+
+// Persistent CTAs (one per SM) walk the tiles (row tile, column tile, K split).  Roles:
+// warp 0 streams digit-plane stages with TMA, warp 1 issues tcgen05.mma, warps 2..9 drain the
+// TMEM accumulators.  Stage, chunk and tile counters run on across tiles so that the loads of the
+// next tile overlap the last MMAs of the current one, and its MMAs overlap the current tile's
+// conversion and stores.
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
         OzParams p) {
@@ -100,13 +151,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // linear tile index: the column tiles of one row tile are adjacent in launch order so that
-  // they share the row tile's digit planes through L2
-  const int ntn = (p.N + BN - 1) / BN;
-  const int n0 = (int)(blockIdx.x % ntn) * BN, m0 = (int)(blockIdx.x / ntn) * BM, z = blockIdx.z;
-  const int kb0 = z * p.kb_per_split;
-  const int nkb = min(p.kb_total, kb0 + p.kb_per_split) - kb0;
-  const int nchunks = (nkb + CHUNK - 1) / CHUNK;
+  const long ntiles = (long)((p.N + BN - 1) / BN) * ((p.M + BM - 1) / BM) * p.ksplit;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
@@ -130,67 +175,91 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   sm100::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (nkb > 0 && warp == 0 && lane == 0) {
+  if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
-    for (int i = 0; i < nkb; ++i) {
-      const int st = i % NSTAGE;
-      if (i >= NSTAGE &&
-          !sm100::mbar_wait(&empty[st], ((i / NSTAGE) - 1) & 1, abort_flag, p.status, LAS_ERR_TIMEOUT))
-        break;
-      uint8_t* sa = smem + st * STAGE_BYTES;
-      sm100::mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
-      const int kx = (kb0 + i) * BK;
-      sm100::tma_load_3d(sa, &tmA, &full[st], kx, m0, 0);
-      sm100::tma_load_3d(sa + A_BYTES, &tmB, &full[st], kx, n0, 0);
+    long gs = 0;
+    bool ok = true;
+    for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int m0, n0, kb0, nkb;
+      tile_coords(p, t, m0, n0, kb0, nkb);
+      for (int i = 0; i < nkb; ++i, ++gs) {
+        const int st = (int)(gs % NSTAGE);
+        if (gs >= NSTAGE && !sm100::mbar_wait(&empty[st], (uint32_t)((gs / NSTAGE) - 1) & 1,
+                                              abort_flag, p.status, LAS_ERR_TIMEOUT)) {
+          ok = false;
+          break;
+        }
+        uint8_t* sa = smem + st * STAGE_BYTES;
+        sm100::mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
+        const int kb = kb0 + i;
+        sm100::tma_load_3d(sa, &tmA, &full[st], 0, kb * p.a_rpad + p.a_row0 + m0, 0);
+        sm100::tma_load_3d(sa + A_BYTES, &tmB, &full[st], 0, kb * p.b_rpad + p.b_row0 + n0, 0);
+      }
     }
     // never leave the CTA with a bulk copy still writing its shared memory
-    for (int i = max(0, nkb - NSTAGE); i < nkb; ++i)
-      sm100::mbar_wait(&full[i % NSTAGE], (i / NSTAGE) & 1, abort_flag, p.status, LAS_ERR_TIMEOUT);
-  } else if (nkb > 0 && warp == 1 && lane == 0) {
+    for (long g = (gs > NSTAGE ? gs - NSTAGE : 0); g < gs; ++g)
+      sm100::mbar_wait(&full[g % NSTAGE], (uint32_t)(g / NSTAGE) & 1, abort_flag, p.status,
+                       LAS_ERR_TIMEOUT);
+  } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
+    long gs = 0, gc = 0;
     bool ok = true;
-    bool tail_started = false;
-    for (int i = 0; i < nkb && ok; ++i) {
-      const int st = i % NSTAGE;
-      if (!sm100::mbar_wait(&full[st], (i / NSTAGE) & 1, abort_flag, p.status, LAS_ERR_TIMEOUT)) {
-        ok = false;
-        break;
-      }
-      sm100::tc_fence_after();
-      const uint32_t sa = sm100::smem_u32(smem + st * STAGE_BYTES);
-      const uint32_t sb = sa + A_BYTES;
-      // tail groups q = 4, 5 into one FP32 accumulator
-      for (int s = 0; s < NDIG; ++s)
-        for (int t = (s >= NEXACT ? 0 : NEXACT - s); s + t <= NDIG - 1; ++t)
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            sm100::mma_bf16(tmem + COL_TAIL, sm100::smem_desc_sw64(sa + s * A_PLANE + kk * 32),
-                            sm100::smem_desc_sw64(sb + t * B_PLANE + kk * 32), IDESC,
-                            tail_started ? 1u : 0u);
-            tail_started = true;
-          }
-      const int c = i / CHUNK;
-      const bool first_in_chunk = (i % CHUNK) == 0;
-      if (first_in_chunk && c > 0) {
-        if (!sm100::mbar_wait(acce, (c - 1) & 1, abort_flag, p.status, LAS_ERR_TIMEOUT)) {
+    for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int m0, n0, kb0, nkb;
+      tile_coords(p, t, m0, n0, kb0, nkb);
+      for (int i = 0; i < nkb; ++i, ++gs) {
+        const int st = (int)(gs % NSTAGE);
+        if (!sm100::mbar_wait(&full[st], (uint32_t)(gs / NSTAGE) & 1, abort_flag, p.status,
+                              LAS_ERR_TIMEOUT)) {
           ok = false;
           break;
         }
         sm100::tc_fence_after();
-      }
-      // exact groups q = 0..3
-      for (int q = 0; q < NEXACT; ++q) {
-        bool started = !first_in_chunk;
-        for (int s = 0; s <= q; ++s)
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            sm100::mma_bf16(tmem + COL_EXACT0 + q * BN,
-                            sm100::smem_desc_sw64(sa + s * A_PLANE + kk * 32),
-                            sm100::smem_desc_sw64(sb + (q - s) * B_PLANE + kk * 32), IDESC,
+        const bool first_in_chunk = (i % CHUNK) == 0;
+        // a new tile reuses every accumulator: wait until the previous tile has been read out
+        if (i == 0 && gc > 0) {
+          if (!sm100::mbar_wait(acce, (uint32_t)(gc - 1) & 1, abort_flag, p.status,
+                                LAS_ERR_TIMEOUT)) {
+            ok = false;
+            break;
+          }
+          sm100::tc_fence_after();
+        }
+        const uint32_t sa = sm100::smem_u32(smem + st * STAGE_BYTES);
+        const uint32_t sb = sa + A_BYTES;
+        // tail weights q = 4, 5 into one FP32 accumulator
+        bool tail_acc = (i > 0);
+        for (int s = 0; s < NDIG; ++s)
+          for (int t2 = (s >= NEXACT ? 0 : NEXACT - s); s + t2 <= NDIG - 1; ++t2) {
+            sm100::mma_bf16(tmem + COL_TAIL, sm100::smem_desc_sw32(sa + s * A_PLANE),
+                            sm100::smem_desc_sw32(sb + t2 * B_PLANE), IDESC, tail_acc ? 1u : 0u);
+            tail_acc = true;
+          }
+        // a later chunk of the same tile: its exact accumulators must have been drained
+        if (first_in_chunk && i > 0) {
+          if (!sm100::mbar_wait(acce, (uint32_t)(gc - 1) & 1, abort_flag, p.status,
+                                LAS_ERR_TIMEOUT)) {
+            ok = false;
+            break;
+          }
+          sm100::tc_fence_after();
+        }
+        // exact weights q = 0..3
+        for (int q = 0; q < NEXACT; ++q) {
+          bool started = !first_in_chunk;
+          for (int s = 0; s <= q; ++s) {
+            sm100::mma_bf16(tmem + COL_EXACT0 + q * BN, sm100::smem_desc_sw32(sa + s * A_PLANE),
+                            sm100::smem_desc_sw32(sb + (q - s) * B_PLANE), IDESC,
                             started ? 1u : 0u);
             started = true;
           }
+        }
+        sm100::mma_commit(&empty[st]);
+        if ((i % CHUNK) == CHUNK - 1 || i == nkb - 1) {
+          sm100::mma_commit(accf);
+          ++gc;
+        }
       }
-      sm100::mma_commit(&empty[st]);
-      if ((i % CHUNK) == CHUNK - 1 || i == nkb - 1) sm100::mma_commit(accf);
     }
     // make sure no MMA is still writing TMEM when the CTA tears down
     sm100::mma_commit(drain);
@@ -199,65 +268,75 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     // ---------------- epilogue (8 warps) ----------------
     const int lq = warp & 3;                 // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;        // columns [half*48, half*48+48)
-    const int row = m0 + lq * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + half * 48;
-    long long acc[48];
+    const float tscale = __int_as_float((127 + 8 * (NEXACT - 1) + p.sh) << 23);  // 2^(24+sh)
+    long gc = 0;
+    bool ok = true;
+    for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int m0, n0, kb0, nkb;
+      tile_coords(p, t, m0, n0, kb0, nkb);
+      const int nchunks = (nkb + CHUNK - 1) / CHUNK;
+      long long acc[48];
 #pragma unroll
-    for (int j = 0; j < 48; ++j) acc[j] = 0;
-    bool ok = nkb > 0;
-    for (int c = 0; c < nchunks && ok; ++c) {
-      if (!sm100::mbar_wait(accf, c & 1, abort_flag, p.status, LAS_ERR_TIMEOUT)) {
-        ok = false;
-        break;
-      }
-      sm100::tc_fence_after();
+      for (int j = 0; j < 48; ++j) acc[j] = 0;
+      for (int c = 0; c < nchunks; ++c, ++gc) {
+        if (!sm100::mbar_wait(accf, (uint32_t)gc & 1, abort_flag, p.status, LAS_ERR_TIMEOUT)) {
+          ok = false;
+          break;
+        }
+        sm100::tc_fence_after();
 #pragma unroll
-      for (int q = 0; q < NEXACT; ++q) {
-        const float up = __int_as_float((127 + 8 * q) << 23);   // 2^(8q)
+        for (int q = 0; q < NEXACT; ++q) {
+          const float up = __int_as_float((127 + 8 * q) << 23);   // 2^(8q)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          uint32_t r[16];
-          sm100::tmem_ld16(tl + COL_EXACT0 + q * BN + j * 16, r);
-          sm100::tmem_wait_ld();
+          for (int j = 0; j < 3; ++j) {
+            uint32_t r[16];
+            sm100::tmem_ld16(tl + COL_EXACT0 + q * BN + j * 16, r);
+            sm100::tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int iv = __float2int_rn(__uint_as_float(r[e]) * up);
-            acc[j * 16 + e] += (long long)iv * (1ll << (8 * (NEXACT - 1 - q)));
+            for (int e = 0; e < 16; ++e) {
+              const int iv = __float2int_rn(__uint_as_float(r[e]) * up);
+              acc[j * 16 + e] += (long long)iv * (1ll << (8 * (NEXACT - 1 - q)));
+            }
           }
         }
+        if (c == nchunks - 1) {
+          // merge the FP32 tail: acc <- acc * 2^sh + rint(tail * 2^(24+sh))
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            uint32_t r[16];
+            sm100::tmem_ld16(tl + COL_TAIL + j * 16, r);
+            sm100::tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              acc[j * 16 + e] = (long long)((unsigned long long)acc[j * 16 + e] << p.sh) +
+                                __float2ll_rn(__uint_as_float(r[e]) * tscale);
+          }
+        }
+        sm100::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) sm100::mbar_arrive(acce);   // TMEM may be overwritten from here on
       }
-      sm100::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) sm100::mbar_arrive(acce);
-    }
-    if (ok) {
-      // merge the FP32 tail and write FP64 results
-      const float tscale = __int_as_float((127 + 8 * (NEXACT - 1) + p.sh) << 23);  // 2^(24+sh)
+      if (!ok) break;
+      // FP64 results (overlaps the next tile's MMAs)
+      const int row = m0 + lq * 32 + lane;
       const int ea = (p.ea && row < p.M) ? p.ea[row] : 0;
       long L = 0, mu = 0;
       if (p.mode == 1) {
         L = row / p.ht_n;
         mu = row - L * p.ht_n;
       }
+      const int z = kb0 / p.kb_per_split;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        uint32_t r[16];
-        sm100::tmem_ld16(tl + COL_TAIL + j * 16, r);
-        sm100::tmem_wait_ld();
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int col = n0 + half * 48 + j * 16 + e;
-          if (row < p.M && col < p.N) {
-            const long long W =
-                (long long)((unsigned long long)acc[j * 16 + e] << p.sh) +
-                __float2ll_rn(__uint_as_float(r[e]) * tscale);
-            const int E = ea + p.eb[col] - 14 - 8 * (NEXACT - 1) - p.sh;
-            const double v = make_double(W, E);
-            if (p.mode == 0)
-              p.out[(long)z * p.zstride + (long)row * p.ldc + col] = v;
-            else
-              p.out[(L * p.ht_op + col) * (long)p.ht_n + mu] = v;
-          }
+      for (int j = 0; j < 48; ++j) {
+        const int col = n0 + half * 48 + j;
+        if (row < p.M && col < p.N) {
+          const int E = ea + p.eb[col] - 14 - 8 * (NEXACT - 1) - p.sh;
+          const double v = make_double(acc[j], E);
+          if (p.mode == 0)
+            p.out[(long)z * p.zstride + (long)row * p.ldc + col] = v;
+          else
+            p.out[(L * p.ht_op + col) * (long)p.ht_n + mu] = v;
         }
       }
     }
@@ -336,31 +415,34 @@ __device__ __forceinline__ unsigned long long absbits(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
 
-// Short rows: one warp per row r < R; exponent e_r with max|x| < 2^e_r and digit planes
-// planes[s*plane + r*Kp + k] for k < K (zero for K <= k < Kp).
+// Short rows: one warp per row r < Rpad (rows >= R are written as zeros); exponent e_r with
+// max|x| < 2^e_r for r < R, digit planes for every k < nkb*BK (zero beyond K).
 template <class Acc>
 __global__ void __launch_bounds__(256)
-k_slice_rows(Acc acc, long R, long K, long Kp, long plane, __nv_bfloat16* planes, int* ex) {
+k_slice_rows(Acc acc, Planes P, int* ex) {
   const long r = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (r >= R) return;
+  if (r >= P.Rpad) return;
+  const bool live = r < P.R;
   unsigned long long mx = 0;
-  for (long k = lane; k < K; k += 32) {
-    const unsigned long long b = absbits(acc(r, k));
-    mx = b > mx ? b : mx;
-  }
+  if (live)
+    for (long k = lane; k < P.K; k += 32) {
+      const unsigned long long b = absbits(acc(r, k));
+      mx = b > mx ? b : mx;
+    }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
     mx = v > mx ? v : mx;
   }
   const int e = exp_of_maxbits(mx);
-  if (lane == 0) ex[r] = e;
-  for (long k = lane; k < Kp; k += 32) {
+  if (lane == 0 && live) ex[r] = e;
+  const long kend = P.nkb * BK;
+  for (long k = lane; k < kend; k += 32) {
     __nv_bfloat16 d[NDIG];
-    digits_of(k < K ? acc(r, k) : 0.0, e, d);
+    digits_of((live && k < P.K) ? acc(r, k) : 0.0, e, d);
 #pragma unroll
-    for (int s = 0; s < NDIG; ++s) planes[s * plane + r * Kp + k] = d[s];
+    for (int s = 0; s < NDIG; ++s) P.p[P.idx(s, r, k)] = d[s];
   }
 }
 
@@ -389,28 +471,28 @@ k_rowmax_long(Acc acc, long K, long seg, unsigned long long* mx) {
   }
 }
 
-// Long rows, pass 2: element-parallel digits (grid covers R x Kp).
+// Long rows, pass 2: element-parallel digits over Rpad x nkb*BK (zeros outside R x K).
 template <class Acc>
 __global__ void __launch_bounds__(256)
-k_digits_long(Acc acc, long R, long K, long Kp, long plane, const unsigned long long* mx,
-              __nv_bfloat16* planes, int* ex) {
+k_digits_long(Acc acc, Planes P, const unsigned long long* mx, int* ex) {
+  const long kend = P.nkb * BK;
   const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (i >= R * Kp) return;
-  const long r = i / Kp, k = i - r * Kp;
-  const int e = exp_of_maxbits(mx[r]);
-  if (k == 0) ex[r] = e;
+  if (i >= P.Rpad * kend) return;
+  const long r = i / kend, k = i - r * kend;
+  const bool live = r < P.R;
+  const int e = live ? exp_of_maxbits(mx[r]) : 0;
+  if (k == 0 && live) ex[r] = e;
   __nv_bfloat16 d[NDIG];
-  digits_of(k < K ? acc(r, k) : 0.0, e, d);
+  digits_of((live && k < P.K) ? acc(r, k) : 0.0, e, d);
 #pragma unroll
-  for (int s = 0; s < NDIG; ++s) planes[s * plane + r * Kp + k] = d[s];
+  for (int s = 0; s < NDIG; ++s) P.p[P.idx(s, r, k)] = d[s];
 }
 
-// Half-transformed rows (L,p) of Ht [R][n]: exponents, row-major digit planes
-// Hd[s][r][k] (k < Kp) and transposed planes HdT[s][k][r] (k < n, r < Rp), in one pass.
-// Block: 32 consecutive rows, 8 warps.
+// Half-transformed rows (L,p) of Ht [R][n]: exponents, digit planes Hd (rows (L,p), K = mu) and
+// the same digits transposed, HdT (rows mu, K = (L,p)), in one pass.  Block: 32 rows, 8 warps.
+// Rows mu >= n of HdT are never written (they stay zero from set-up).
 __global__ void __launch_bounds__(256)
-k_slice_ht(const double* __restrict__ Ht, long R, int n, long Kp, long plane,
-           __nv_bfloat16* __restrict__ Hd, long Rp, long planeT, __nv_bfloat16* __restrict__ HdT,
+k_slice_ht(const double* __restrict__ Ht, long R, int n, Planes Hd, Planes HdT,
            int* __restrict__ ex) {
   __shared__ __nv_bfloat16 tile[NDIG][32][34];
   __shared__ int es[32];
@@ -436,7 +518,8 @@ k_slice_ht(const double* __restrict__ Ht, long R, int n, long Kp, long plane,
     }
   }
   __syncthreads();
-  for (long k0 = 0; k0 < Kp; k0 += 32) {
+  const long kend = Hd.nkb * BK;
+  for (long k0 = 0; k0 < kend; k0 += 32) {
     for (int i = 0; i < 4; ++i) {
       const int row = warp + 8 * i;
       const long r = r0 + row, k = k0 + lane;
@@ -445,16 +528,16 @@ k_slice_ht(const double* __restrict__ Ht, long R, int n, long Kp, long plane,
 #pragma unroll
       for (int s = 0; s < NDIG; ++s) {
         tile[s][row][lane] = d[s];
-        if (r < R && k < Kp) Hd[s * plane + r * Kp + k] = d[s];
+        if (r < Hd.Rpad && k < kend) Hd.p[Hd.idx(s, r, k)] = d[s];
       }
     }
     __syncthreads();
     for (int i = 0; i < 4; ++i) {
       const int kk = warp * 4 + i;
       const long k = k0 + kk, r = r0 + lane;
-      if (k < n && r < Rp) {
+      if (k < n && r < HdT.nkb * BK) {
 #pragma unroll
-        for (int s = 0; s < NDIG; ++s) HdT[s * planeT + k * Rp + r] = tile[s][lane][kk];
+        for (int s = 0; s < NDIG; ++s) HdT.p[HdT.idx(s, k, r)] = tile[s][lane][kk];
       }
     }
     __syncthreads();
@@ -486,18 +569,19 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3D map over digit planes [NDIG][rows][Kp] (BF16), box {BK, box_rows, NDIG}, 64-byte swizzle.
-static las_status make_plane_map(CUtensorMap* m, const void* base, long rows, long Kp,
-                                 long plane_stride_elems, int box_rows) {
+// 3D map over K-blocked digit planes: dims {BK, nkb*Rpad, NDIG}, box {BK, box_rows, NDIG},
+// 32-byte swizzle.  Each box is box_rows * 32 contiguous bytes per plane.
+static las_status make_plane_map(CUtensorMap* m, const Planes& P, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return LAS_ERR_CUDA;
-  if (((uintptr_t)base & 15) || (Kp % 8) || rows <= 0 || rows > 0xFFFFFFFFL) return LAS_ERR_INTERNAL;
-  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)NDIG};
-  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)plane_stride_elems * 2};
+  const long rows = P.nkb * P.Rpad;
+  if (((uintptr_t)P.p & 15) || rows <= 0 || rows > 0x7FFFFFFFL) return LAS_ERR_INTERNAL;
+  cuuint64_t dims[3] = {(cuuint64_t)BK, (cuuint64_t)rows, (cuuint64_t)NDIG};
+  cuuint64_t strides[2] = {(cuuint64_t)BK * 2, (cuuint64_t)P.plane * 2};
   cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)NDIG};
   cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
-                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)P.p, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? LAS_OK : LAS_ERR_INTERNAL;
 }
@@ -517,26 +601,34 @@ static las_status ozaki_prepare() {
 
 static inline long rup(long x, long m) { return (x + m - 1) / m * m; }
 
-// out = A * B^T where A planes [NDIG][M][Kp] (row exponents ea) and B planes [NDIG][N][Kp]
-// (row exponents eb = column exponents of the product).  plane strides are in elements.
-las_status ozaki_gemm(const __nv_bfloat16* Ad, long a_plane, const int* ea, long M,
-                      const __nv_bfloat16* Bd, long b_plane, const int* eb, long N, long K,
-                      long Kp, int ksplit, int mode, double* out, long ldc, long zstride,
-                      int ht_n, int ht_op, int* status, cudaStream_t st) {
+// out = A * B^T over K: rows [a_row0, a_row0 + M) of A (row exponents ea, or 0 when null),
+// rows [b_row0, b_row0 + N) of B (row exponents eb: the column exponents of the product).
+// mode 0: out[z*zstride + r*ldc + c] (z = K split); mode 1: Ht layout (rows (L, mu)).
+las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const Planes& B,
+                      long b_row0, const int* eb, long N, long K, int ksplit, int mode,
+                      double* out, long ldc, long zstride, int ht_n, int ht_op, int* status,
+                      cudaStream_t st) {
   if (M <= 0 || N <= 0) return LAS_OK;
+  if (a_row0 + M > A.Rpad || b_row0 + N > B.Rpad || K > A.nkb * BK || K > B.nkb * BK)
+    return LAS_ERR_INTERNAL;
   las_status s = ozaki_prepare();
   if (s != LAS_OK) return s;
   CUtensorMap ma, mb;
-  if ((s = make_plane_map(&ma, Ad, M, Kp, a_plane, BM)) != LAS_OK) return s;
-  if ((s = make_plane_map(&mb, Bd, N, Kp, b_plane, BN)) != LAS_OK) return s;
+  if ((s = make_plane_map(&ma, A, BM)) != LAS_OK) return s;
+  if ((s = make_plane_map(&mb, B, BN)) != LAS_OK) return s;
   OzParams p;
   p.M = (int)M;
   p.N = (int)N;
+  p.a_rpad = (int)A.Rpad;
+  p.b_rpad = (int)B.Rpad;
+  p.a_row0 = (int)a_row0;
+  p.b_row0 = (int)b_row0;
   p.kb_total = (int)((K + BK - 1) / BK);
   if (p.kb_total < 1) p.kb_total = 1;
   if (ksplit < 1) ksplit = 1;
   p.kb_per_split = (p.kb_total + ksplit - 1) / ksplit;
   ksplit = (p.kb_total + p.kb_per_split - 1) / p.kb_per_split;
+  p.ksplit = ksplit;
   p.ea = ea;
   p.eb = eb;
   p.out = out;
@@ -550,9 +642,15 @@ las_status ozaki_gemm(const __nv_bfloat16* Ad, long a_plane, const int* ea, long
   while ((1L << lgk) < (long)p.kb_per_split * BK) ++lgk;
   p.sh = std::max(0, std::min(20, 61 - 14 - 8 * (NEXACT - 1) - lgk));
   p.status = status;
-  const long tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
-  if (tiles > 0x7FFFFFFFL || ksplit > 65535) return LAS_ERR_UNSUPPORTED;
-  dim3 grid((unsigned)tiles, 1, (unsigned)ksplit);
+  const long tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM) * (long)ksplit;
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+      nsm = 148;
+  }
+  dim3 grid((unsigned)std::min<long>(tiles, nsm), 1, 1);   // persistent: one CTA per SM
   k_ozaki<<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, p);
   las_count_launch();
   cudaError_t e = cudaGetLastError();
@@ -564,28 +662,26 @@ las_status ozaki_gemm(const __nv_bfloat16* Ad, long a_plane, const int* ea, long
 }
 
 template <class Acc>
-static las_status slice_rows(Acc acc, long R, long K, long Kp, long plane, __nv_bfloat16* planes,
-                             int* ex, cudaStream_t st, unsigned long long* mx_ws = nullptr) {
-  if (R <= 0) return LAS_OK;
-  if (K > 8192 && mx_ws && R <= 65535) {
+static las_status slice_rows(Acc acc, const Planes& P, int* ex, cudaStream_t st,
+                             unsigned long long* mx_ws = nullptr) {
+  if (P.R <= 0) return LAS_OK;
+  if (P.K > 8192 && mx_ws && P.R <= 65535) {
     // long rows: block-parallel maxima, then element-parallel digits
-    cudaError_t e0 = cudaMemsetAsync(mx_ws, 0, R * sizeof(unsigned long long), st);
+    cudaError_t e0 = cudaMemsetAsync(mx_ws, 0, P.R * sizeof(unsigned long long), st);
     if (e0 != cudaSuccess) {
       las_record_cuda_error(e0, "cudaMemsetAsync(rowmax)", __FILE__, __LINE__);
       return LAS_ERR_CUDA;
     }
     const long seg = 8192;
-    dim3 g1((unsigned)((K + seg - 1) / seg), (unsigned)R);
-    k_rowmax_long<Acc><<<g1, 256, 0, st>>>(acc, K, seg, mx_ws);
+    dim3 g1((unsigned)((P.K + seg - 1) / seg), (unsigned)P.R);
+    k_rowmax_long<Acc><<<g1, 256, 0, st>>>(acc, P.K, seg, mx_ws);
     las_count_launch();
-    const long tot = R * Kp;
-    k_digits_long<Acc><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(acc, R, K, Kp, plane,
-                                                                      mx_ws, planes, ex);
+    const long tot = P.Rpad * P.nkb * BK;
+    k_digits_long<Acc><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(acc, P, mx_ws, ex);
     las_count_launch();
   } else {
-    const long threads = R * 32;
-    k_slice_rows<Acc><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(acc, R, K, Kp, plane,
-                                                                          planes, ex);
+    const long threads = P.Rpad * 32;
+    k_slice_rows<Acc><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(acc, P, ex);
     las_count_launch();
   }
   cudaError_t e = cudaGetLastError();
@@ -598,37 +694,35 @@ static las_status slice_rows(Acc acc, long R, long K, long Kp, long plane, __nv_
 
 struct SplitState {
   int n, X, op, Lc;
-  long Kp;          // padded AO dimension
-  long Rp;          // padded Lc*op
-  __nv_bfloat16* Bdig;   // [NDIG][X*n][Kp]
+  Planes Bdig;           // rows (L, mu) of all X*n, K = nu
   int* Bexp;             // [X*n]
-  __nv_bfloat16* Cdig;   // [NDIG][op][Kp]
+  Planes Cdig;           // rows p of C_occ^T, K = nu
   int* Cexp;             // [op]
-  __nv_bfloat16* Hdig;   // [NDIG][Lc*op][Kp]
+  Planes Hdig;           // rows (L, p) of a chunk, K = mu
   int* Hexp;             // [Lc*op]
-  __nv_bfloat16* HdigT;  // [NDIG][n][Rp]
-  __nv_bfloat16* Wdig;   // [NDIG][op][Rp]
+  Planes HdigT;          // rows mu, K = (L, p)
+  Planes Wdig;           // rows q, K = (L, p)
   int* Wexp;             // [op]
   double* part;          // [ksplit][n][op]
   unsigned long long* mx;  // [op] row maxima for long-row slicing
-  __nv_bfloat16* hdig;   // [NDIG][n][Kp]   one-electron h
+  Planes hdig;           // rows mu of h, K = nu
   int* hexp;             // [n]
-  __nv_bfloat16* hcdig;  // [NDIG][op][Kp]  columns of h C_occ
+  Planes hcdig;          // rows q of (h C_occ)^T, K = mu
   int* hcexp;            // [op]
   int ksplit6;
   int* status;
 };
 
 static void split_free(SplitState* s) {
-  void* ptrs[] = {s->Bdig, s->Bexp, s->Cdig, s->Cexp, s->Hdig, s->Hexp, s->HdigT, s->Wdig,
-                  s->Wexp, s->part, s->mx, s->hdig, s->hexp, s->hcdig, s->hcexp};
+  void* ptrs[] = {s->Bdig.p, s->Bexp, s->Cdig.p, s->Cexp, s->Hdig.p, s->Hexp, s->HdigT.p,
+                  s->Wdig.p, s->Wexp, s->part, s->mx, s->hdig.p, s->hexp, s->hcdig.p, s->hcexp};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
 
 size_t split_bytes_per_aux(int n, int op) {
-  const long Kp = rup(n, 8);
-  return (size_t)NDIG * op * Kp * 2 * 2 + (size_t)NDIG * op * op * 2 + (size_t)op * 4;
+  // Hdig + HdigT + Wdig per auxiliary index (K-blocked, padded), plus exponents
+  return (size_t)NDIG * op * rup(n, BK) * 2 * 2 + (size_t)NDIG * ROWPAD * op * 2 + (size_t)op * 4;
 }
 
 las_status split_create(SplitState** out, int n, int X, int op, int Lc, const double* Bp,
@@ -641,8 +735,6 @@ las_status split_create(SplitState** out, int n, int X, int op, int Lc, const do
   s->X = X;
   s->op = op;
   s->Lc = Lc;
-  s->Kp = rup(n, 8);
-  s->Rp = rup((long)Lc * op, 8);
   s->status = status;
   {
     const long tiles = ((n + BM - 1) / BM) * ((op + BN - 1) / BN);
@@ -660,26 +752,35 @@ las_status split_create(SplitState** out, int n, int X, int op, int Lc, const do
     }
     total += b;
   };
-  const long XN = (long)X * n;
-  A((void**)&s->Bdig, (size_t)NDIG * XN * s->Kp * 2);
+  const long XN = (long)X * n, R = (long)Lc * op;
+  void* q = nullptr;
+  A(&q, planes_bytes(XN, n));        s->Bdig = make_planes(q, XN, n);   q = nullptr;
   A((void**)&s->Bexp, (size_t)XN * 4);
-  A((void**)&s->Cdig, (size_t)NDIG * op * s->Kp * 2);
+  A(&q, planes_bytes(op, n));        s->Cdig = make_planes(q, op, n);   q = nullptr;
   A((void**)&s->Cexp, (size_t)op * 4);
-  A((void**)&s->Hdig, (size_t)NDIG * Lc * op * s->Kp * 2);
-  A((void**)&s->Hexp, (size_t)s->Rp * 4);
-  A((void**)&s->HdigT, (size_t)NDIG * n * s->Rp * 2);
-  A((void**)&s->Wdig, (size_t)NDIG * op * s->Rp * 2);
+  A(&q, planes_bytes(R, n));         s->Hdig = make_planes(q, R, n);    q = nullptr;
+  A((void**)&s->Hexp, (size_t)R * 4);
+  A(&q, planes_bytes(n, R));         s->HdigT = make_planes(q, n, R);   q = nullptr;
+  A(&q, planes_bytes(op, R));        s->Wdig = make_planes(q, op, R);   q = nullptr;
   A((void**)&s->Wexp, (size_t)op * 4);
   A((void**)&s->part, (size_t)s->ksplit6 * n * op * 8);
   A((void**)&s->mx, (size_t)op * 8);
-  A((void**)&s->hdig, (size_t)NDIG * n * s->Kp * 2);
+  A(&q, planes_bytes(n, n));         s->hdig = make_planes(q, n, n);    q = nullptr;
   A((void**)&s->hexp, (size_t)n * 4);
-  A((void**)&s->hcdig, (size_t)NDIG * op * s->Kp * 2);
+  A(&q, planes_bytes(op, n));        s->hcdig = make_planes(q, op, n);  q = nullptr;
   A((void**)&s->hcexp, (size_t)op * 4);
+  if (rc == LAS_OK) {
+    // rows mu >= n of the transposed planes are never written: make them zero once
+    cudaError_t e = cudaMemsetAsync(s->HdigT.p, 0, planes_bytes(n, R), st);
+    if (e != cudaSuccess) {
+      las_record_cuda_error(e, "cudaMemsetAsync(HdigT)", __FILE__, __LINE__);
+      rc = LAS_ERR_CUDA;
+    }
+  }
   if (rc == LAS_OK) {
     // one-time digit planes of the Cholesky vectors: rows (L, mu), K = nu
     RowsPacked acc{Bp, (long)n * (n + 1) / 2, n};
-    rc = slice_rows(acc, XN, n, s->Kp, XN * s->Kp, s->Bdig, s->Bexp, st);
+    rc = slice_rows(acc, s->Bdig, s->Bexp, st);
   }
   if (rc != LAS_OK) {
     split_free(s);
@@ -702,23 +803,21 @@ const int* split_hexp(SplitState* s) { return s->Hexp; }
 las_status split_prepare_C(SplitState* s, const double* Cocc, cudaStream_t st) {
   // rows p of C_occ^T (K = nu): element (p, nu) = Cocc[nu*op + p]
   RowsStrided acc{Cocc, 1, s->op, nullptr};
-  return slice_rows(acc, s->op, s->n, s->Kp, (long)s->op * s->Kp, s->Cdig, s->Cexp, st);
+  return slice_rows(acc, s->Cdig, s->Cexp, st);
 }
 
 las_status split_half(SplitState* s, int l0, int nL, double* Ht, cudaStream_t st) {
   const long rows = (long)nL * s->n;
-  const long plane = (long)s->X * s->n * s->Kp;
-  return ozaki_gemm(s->Bdig + (long)l0 * s->n * s->Kp, plane, s->Bexp + (long)l0 * s->n, rows,
-                    s->Cdig, (long)s->op * s->Kp, s->Cexp, s->op, s->n, s->Kp, 1, 1, Ht, 0, 0,
-                    s->n, s->op, s->status, st);
+  return ozaki_gemm(s->Bdig, (long)l0 * s->n, s->Bexp + (long)l0 * s->n, rows, s->Cdig, 0,
+                    s->Cexp, s->op, s->n, 1, 1, Ht, 0, 0, s->n, s->op, s->status, st);
 }
 
 las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaStream_t st) {
   const long R = (long)nL * s->op;
-  const long Rp = rup(R, 8);
-  k_slice_ht<<<(unsigned)((Rp + 31) / 32), 256, 0, st>>>(Ht, R, s->n, s->Kp,
-                                                         (long)s->Lc * s->op * s->Kp, s->Hdig, Rp,
-                                                         (long)s->n * Rp, s->HdigT, s->Hexp);
+  // chunk views: same allocations, the chunk's own K extent for the transposed planes
+  Planes HdT = s->HdigT;
+  HdT.K = R;
+  k_slice_ht<<<(unsigned)((R + 31) / 32), 256, 0, st>>>(Ht, R, s->n, s->Hdig, HdT, s->Hexp);
   las_count_launch();
   {
     cudaError_t e = cudaGetLastError();
@@ -727,23 +826,23 @@ las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaSt
       return LAS_ERR_CUDA;
     }
   }
-  return ozaki_gemm(s->Hdig, (long)s->Lc * s->op * s->Kp, s->Hexp, R, s->Cdig,
-                    (long)s->op * s->Kp, s->Cexp, s->op, s->n, s->Kp, 1, 0, T, s->op, 0, 0, 0,
-                    s->status, st);
+  return ozaki_gemm(s->Hdig, 0, s->Hexp, R, s->Cdig, 0, s->Cexp, s->op, s->n, 1, 0, T, s->op, 0,
+                    0, 0, s->status, st);
 }
 
 las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, int accumulate,
                          cudaStream_t st) {
-  const long R = (long)nL * s->op;      // K of the projection: (L, p)
-  const long Rp = rup(R, 8);
+  const long R = (long)nL * s->op;      // K of the projection: (L, p); a multiple of 16
   // the transposed digit planes of H (HdigT) were written by split_full
   // W rows q (K = (L,p)), already scaled by 2^Hexp[(L,p)] and stored transposed: Wt[q][R]
+  Planes W = s->Wdig;
+  W.K = R;
   RowsStrided acc{Wt, R, 1, nullptr};
-  las_status rc = slice_rows(acc, s->op, R, Rp, (long)s->op * Rp, s->Wdig, s->Wexp, st, s->mx);
+  las_status rc = slice_rows(acc, W, s->Wexp, st, s->mx);
   if (rc != LAS_OK) return rc;
   const int ks = (int)std::max(1L, std::min((long)s->ksplit6, (R + 32 * 64 - 1) / (32 * 64)));
-  rc = ozaki_gemm(s->HdigT, (long)s->n * Rp, nullptr, s->n, s->Wdig, (long)s->op * Rp, s->Wexp,
-                  s->op, R, Rp, ks, 0, s->part, s->op, (long)s->n * s->op, 0, 0, s->status, st);
+  rc = ozaki_gemm(s->HdigT, 0, nullptr, s->n, W, 0, s->Wexp, s->op, R, ks, 0, s->part, s->op,
+                  (long)s->n * s->op, 0, 0, s->status, st);
   if (rc != LAS_OK) return rc;
   launch_reduce_partials(s->part, ks, (long)s->n * s->op, Out, accumulate, st);
   return LAS_OK;
@@ -752,18 +851,16 @@ las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, i
 las_status split_one_electron(SplitState* s, const double* h, double* hC, double* hmo,
                               cudaStream_t st) {
   // hC = h C_occ  (rows mu of h, columns p of C_occ: the digits of C_occ are already sliced)
-  las_status rc = slice_rows(RowsStrided{h, s->n, 1, nullptr}, s->n, s->n, s->Kp,
-                             (long)s->n * s->Kp, s->hdig, s->hexp, st);
+  las_status rc = slice_rows(RowsStrided{h, s->n, 1, nullptr}, s->hdig, s->hexp, st);
   if (rc == LAS_OK)
-    rc = ozaki_gemm(s->hdig, (long)s->n * s->Kp, s->hexp, s->n, s->Cdig, (long)s->op * s->Kp,
-                    s->Cexp, s->op, s->n, s->Kp, 1, 0, hC, s->op, 0, 0, 0, s->status, st);
+    rc = ozaki_gemm(s->hdig, 0, s->hexp, s->n, s->Cdig, 0, s->Cexp, s->op, s->n, 1, 0, hC, s->op,
+                    0, 0, 0, s->status, st);
   // hmo = C_occ^T hC  (rows p of C_occ^T are the C_occ digit rows; columns q of hC)
   if (rc == LAS_OK)
-    rc = slice_rows(RowsStrided{hC, 1, s->op, nullptr}, s->op, s->n, s->Kp, (long)s->op * s->Kp,
-                    s->hcdig, s->hcexp, st);
+    rc = slice_rows(RowsStrided{hC, 1, s->op, nullptr}, s->hcdig, s->hcexp, st);
   if (rc == LAS_OK)
-    rc = ozaki_gemm(s->Cdig, (long)s->op * s->Kp, s->Cexp, s->op, s->hcdig, (long)s->op * s->Kp,
-                    s->hcexp, s->op, s->n, s->Kp, 1, 0, hmo, s->op, 0, 0, 0, s->status, st);
+    rc = ozaki_gemm(s->Cdig, 0, s->Cexp, s->op, s->hcdig, 0, s->hcexp, s->op, s->n, 1, 0, hmo,
+                    s->op, 0, 0, 0, s->status, st);
   return rc;
 }
 
@@ -771,8 +868,8 @@ las_status split_one_electron(SplitState* s, const double* h, double* hC, double
 // Standalone emulated-FP64 GEMM through the same kernels (C ABI)
 // ------------------------------------------------------------------------------------------
 static size_t sgemm_ws(long M, long N, long K) {
-  const long Kp = rup(K, 8);
-  return (size_t)NDIG * (M + N) * Kp * 2 + (size_t)(M + N) * 4 + 4096;
+  return rup(planes_bytes(M, K), 256) + rup(planes_bytes(N, K), 256) + rup(M * 4, 256) +
+         rup(N * 4, 256) + 256;
 }
 
 extern "C" size_t las_split_gemm_workspace(long M, long N, long K) {
@@ -785,33 +882,31 @@ extern "C" las_status las_split_gemm(long M, long N, long K, const double* A, lo
                                      void* workspace, size_t workspace_bytes, void* stream) {
   if (M < 0 || N < 0 || K < 0) return LAS_ERR_ARG;
   if (M == 0 || N == 0) return LAS_OK;
-  if (!A || !B || !C || !workspace) return LAS_ERR_ARG;
+  if (!A || !B || !C) return LAS_ERR_ARG;
   if (lda < K || ldb < N || ldc < N) return LAS_ERR_ARG;
-  if (workspace_bytes < sgemm_ws(M, N, K) || ((uintptr_t)workspace & 255)) return LAS_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
   if (K == 0) {
-    cudaStream_t st = (cudaStream_t)stream;
     for (long r = 0; r < M; ++r)
       LAS_CUDA_TRY(cudaMemsetAsync(C + r * ldc, 0, N * 8, st));
     return LAS_OK;
   }
-  cudaStream_t st = (cudaStream_t)stream;
-  const long Kp = rup(K, 8);
+  if (!workspace) return LAS_ERR_ARG;
+  if (workspace_bytes < sgemm_ws(M, N, K) || ((uintptr_t)workspace & 255)) return LAS_ERR_WORKSPACE;
   uint8_t* w = (uint8_t*)workspace;
-  __nv_bfloat16* Ad = (__nv_bfloat16*)w;
-  w += rup((long)NDIG * M * Kp * 2, 256);
-  __nv_bfloat16* Bd = (__nv_bfloat16*)w;
-  w += rup((long)NDIG * N * Kp * 2, 256);
+  Planes Ad = make_planes(w, M, K);
+  w += rup(planes_bytes(M, K), 256);
+  Planes Bd = make_planes(w, N, K);
+  w += rup(planes_bytes(N, K), 256);
   int* ea = (int*)w;
   w += rup(M * 4, 256);
   int* eb = (int*)w;
   w += rup(N * 4, 256);
   int* status = (int*)w;
   LAS_CUDA_TRY(cudaMemsetAsync(status, 0, 4, st));
-  las_status rc = slice_rows(RowsStrided{A, lda, 1, nullptr}, M, K, Kp, M * Kp, Ad, ea, st);
+  las_status rc = slice_rows(RowsStrided{A, lda, 1, nullptr}, Ad, ea, st);
+  if (rc == LAS_OK) rc = slice_rows(RowsStrided{B, 1, ldb, nullptr}, Bd, eb, st);
   if (rc == LAS_OK)
-    rc = slice_rows(RowsStrided{B, 1, ldb, nullptr}, N, K, Kp, N * Kp, Bd, eb, st);
-  if (rc == LAS_OK)
-    rc = ozaki_gemm(Ad, M * Kp, ea, M, Bd, N * Kp, eb, N, K, Kp, 1, 0, C, ldc, 0, 0, 0, status, st);
+    rc = ozaki_gemm(Ad, 0, ea, M, Bd, 0, eb, N, K, 1, 0, C, ldc, 0, 0, 0, status, st);
   if (rc != LAS_OK) return rc;
   int h = 0;
   LAS_CUDA_TRY(cudaMemcpyAsync(&h, status, 4, cudaMemcpyDeviceToHost, st));

@@ -143,6 +143,17 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
   return d;
 }
 
+// The same for 32-byte rows (16 BF16) in the 32-byte swizzle mode; 8-row groups 256 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused here)
+  d |= (uint64_t)(256 >> 4) << 32;                 // stride byte offset: 8 rows x 32 B
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)6 << 61;                          // swizzle: 32-byte
+  return d;
+}
+
 // Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
