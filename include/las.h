@@ -64,9 +64,10 @@ typedef struct {
 } las_dims;
 
 /* Create a context over the packed Cholesky vectors B_packed (device, naux*nao(nao+1)/2
- * doubles).  The context keeps a reference to B_packed (it must stay valid and unchanged until
- * las_destroy); in LAS_SPLIT_BF16 mode it also builds, once, the digit planes of B it needs
- * (owned by the context).  max_workspace_bytes caps the per-evaluation workspace (0 = choose);
+ * doubles).  In LAS_FP64 mode the context keeps a reference to B_packed, which must stay valid
+ * and unchanged until las_destroy.  In LAS_SPLIT_BF16 mode it builds, once, the digit planes of
+ * B (owned by the context); afterwards B_packed is read only by las_df_jk, so a caller that
+ * never calls las_df_jk may free it after las_create returns.  max_workspace_bytes caps the per-evaluation workspace (0 = choose);
  * the auxiliary index is processed in chunks that fit it.  stream: a cudaStream_t (NULL = the
  * legacy default stream).  Synchronous with respect to the set-up work. */
 las_status las_create(las_ctx** ctx, const las_dims* dims, const double* B_packed,
@@ -120,6 +121,30 @@ las_status las_energy_grad(las_ctx* ctx, const double* C, const double* h, const
 las_status las_energy_grad_host(las_ctx* ctx, const double* C_host, const double* h_host,
                                 const double* dm1s_host, const double* dm2_host,
                                 double* E_host, double* dEdC_host);
+
+/* One item of a batched evaluation: device pointers as for las_energy_grad (dEdC required). */
+typedef struct {
+  const double* C;
+  const double* h;
+  const double* dm1s;
+  const double* dm2;
+  double* E;
+  double* dEdC;
+} las_batch_item;
+
+/* Evaluate nsys independent problems (item i on ctxs[i], all distinct contexts) as one CUDA
+ * graph on `stream`: the first call with a given list of contexts, item pointers and stream
+ * captures every problem's chain of kernels; later calls with the same arguments replay the
+ * captured graph with a single launch.  Inputs may change between calls (the pointers may not).
+ * A graph is dropped when any of its contexts is destroyed.  Asynchronous. */
+las_status las_energy_grad_batched(int nsys, las_ctx* const* ctxs, const las_batch_item* items,
+                                   void* stream);
+
+/* Autotuner: times one full evaluation per candidate split-K factor of the projection GEMM
+ * (S5/S6) and keeps the fastest for this context (split mode; no-op in FP64 mode).  Writes E and
+ * dEdC as a side effect.  Synchronous. */
+las_status las_autotune(las_ctx* ctx, const double* C, const double* h, const double* dm1s,
+                        const double* dm2, double* E, double* dEdC);
 
 /* Per-stage device times (milliseconds), averaged over the evaluations run since timing was
  * enabled with las_set_timing(ctx, 1) or since the last las_stage_times call (up to the last

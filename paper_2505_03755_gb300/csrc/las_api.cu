@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "gemm_f64.cuh"
@@ -241,9 +242,34 @@ extern "C" las_status las_create(las_ctx** out, const las_dims* d, const double*
   return LAS_OK;
 }
 
+// Captured batched evaluations, keyed by (contexts, item pointers, stream).
+struct GraphEntry {
+  std::vector<las_ctx*> ctxs;
+  std::vector<las_batch_item> items;
+  cudaStream_t stream;
+  cudaGraphExec_t exec;
+};
+static std::mutex g_graph_mu;
+static std::vector<GraphEntry> g_graphs;
+
+static void drop_graphs_of(las_ctx* x) {
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  for (size_t i = 0; i < g_graphs.size();) {
+    bool hit = false;
+    for (las_ctx* c : g_graphs[i].ctxs) hit |= (c == x);
+    if (hit) {
+      cudaGraphExecDestroy(g_graphs[i].exec);
+      g_graphs.erase(g_graphs.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
 extern "C" las_status las_destroy(las_ctx* x) {
   if (!x) return LAS_ERR_ARG;
   cudaStreamSynchronize(x->stream);
+  drop_graphs_of(x);
   free_all(x);
   free(x);
   return LAS_OK;
@@ -522,4 +548,118 @@ extern "C" las_status las_df_transform(las_ctx* x, const double* C, int p0, int 
     if ((st = check_launch()) != LAS_OK) return st;
   }
   return LAS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Batched evaluation under one captured CUDA graph
+// ------------------------------------------------------------------------------------------
+static bool same_items(const las_batch_item& a, const las_batch_item& b) {
+  return a.C == b.C && a.h == b.h && a.dm1s == b.dm1s && a.dm2 == b.dm2 && a.E == b.E &&
+         a.dEdC == b.dEdC;
+}
+
+extern "C" las_status las_energy_grad_batched(int nsys, las_ctx* const* ctxs,
+                                              const las_batch_item* items, void* stream) {
+  if (nsys < 0 || (nsys > 0 && (!ctxs || !items))) return LAS_ERR_ARG;
+  if (nsys == 0) return LAS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < nsys; ++i) {
+    if (!ctxs[i] || !items[i].C || !items[i].h || !items[i].E || !items[i].dEdC) return LAS_ERR_ARG;
+    if (ctxs[i]->a > 0 && (!items[i].dm1s || !items[i].dm2)) return LAS_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return LAS_ERR_ARG;   // a context's workspace serves one item
+  }
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  for (GraphEntry& g : g_graphs) {
+    if (g.stream != st || (int)g.ctxs.size() != nsys) continue;
+    bool match = true;
+    for (int i = 0; i < nsys && match; ++i)
+      match = g.ctxs[i] == ctxs[i] && same_items(g.items[i], items[i]);
+    if (match) {
+      LAS_CUDA_TRY(cudaGraphLaunch(g.exec, st));
+      return LAS_OK;
+    }
+  }
+  // capture every system's chain, in order, on a private stream (the caller's stream may be the
+  // legacy default stream, which cannot be captured); the graph is then launched on `st`
+  static cudaStream_t cap_stream[64];
+  int dev = 0;
+  LAS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return LAS_ERR_UNSUPPORTED;
+  if (!cap_stream[dev]) LAS_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream[dev], cudaStreamNonBlocking));
+  cudaStream_t cs = cap_stream[dev];
+  LAS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  las_status rc = LAS_OK;
+  for (int i = 0; i < nsys && rc == LAS_OK; ++i) {
+    las_ctx* x = ctxs[i];
+    cudaStream_t saved = x->stream;
+    const int timing = x->timing;
+    x->stream = cs;
+    x->timing = 0;
+    rc = evaluate(x, items[i].C, items[i].h, items[i].dm1s, items[i].dm2, items[i].E,
+                  items[i].dEdC, nullptr);
+    x->stream = saved;
+    x->timing = timing;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  if (rc != LAS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    return LAS_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+    return LAS_ERR_CUDA;
+  }
+  GraphEntry g;
+  g.ctxs.assign(ctxs, ctxs + nsys);
+  g.items.assign(items, items + nsys);
+  g.stream = st;
+  g.exec = exec;
+  g_graphs.push_back(g);
+  LAS_CUDA_TRY(cudaGraphLaunch(exec, st));
+  return LAS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Autotuner: the split-K factor of the projection GEMM, chosen by timing
+// ------------------------------------------------------------------------------------------
+extern "C" las_status las_autotune(las_ctx* x, const double* C, const double* h,
+                                   const double* dm1s, const double* dm2, double* E,
+                                   double* dEdC) {
+  if (!x || !C || !h || !E || !dEdC) return LAS_ERR_ARG;
+  if (x->prec != LAS_SPLIT_BF16) return LAS_OK;   // the FP64 path is bound by FP64 arithmetic
+  las_status st = las_set_timing(x, 1);
+  if (st != LAS_OK) return st;
+  const int cands[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+  int best = split_get_ksplit(x->split);
+  float best_ms = 1e30f;
+  for (int ks : cands) {
+    split_set_ksplit(x->split, ks);
+    // two runs: the second is timed
+    for (int r = 0; r < 2; ++r) {
+      if ((st = evaluate(x, C, h, dm1s, dm2, E, dEdC, nullptr)) != LAS_OK) break;
+      if (r == 0) {
+        float dummy[8];
+        las_stage_times(x, dummy, 8);
+      }
+    }
+    if (st != LAS_OK) break;
+    float ms[8] = {0};
+    if (las_stage_times(x, ms, 8) >= 4 && ms[3] < best_ms) {
+      best_ms = ms[3];
+      best = ks;
+    }
+  }
+  split_set_ksplit(x->split, best);
+  las_set_timing(x, 0);
+  if (st != LAS_OK) return st;
+  return las_sync(x);
 }

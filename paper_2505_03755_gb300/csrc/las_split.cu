@@ -601,6 +601,17 @@ static las_status ozaki_prepare() {
 
 static inline long rup(long x, long m) { return (x + m - 1) / m * m; }
 
+static int num_sms() {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+      nsm = 148;
+  }
+  return nsm;
+}
+
 // out = A * B^T over K: rows [a_row0, a_row0 + M) of A (row exponents ea, or 0 when null),
 // rows [b_row0, b_row0 + N) of B (row exponents eb: the column exponents of the product).
 // mode 0: out[z*zstride + r*ldc + c] (z = K split); mode 1: Ht layout (rows (L, mu)).
@@ -643,14 +654,7 @@ las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const
   p.sh = std::max(0, std::min(20, 61 - 14 - 8 * (NEXACT - 1) - lgk));
   p.status = status;
   const long tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM) * (long)ksplit;
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
-      nsm = 148;
-  }
-  dim3 grid((unsigned)std::min<long>(tiles, nsm), 1, 1);   // persistent: one CTA per SM
+  dim3 grid((unsigned)std::min<long>(tiles, num_sms()), 1, 1);   // persistent: one CTA per SM
   k_ozaki<<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, p);
   las_count_launch();
   cudaError_t e = cudaGetLastError();
@@ -709,7 +713,8 @@ struct SplitState {
   int* hexp;             // [n]
   Planes hcdig;          // rows q of (h C_occ)^T, K = mu
   int* hcexp;            // [op]
-  int ksplit6;
+  int ksplit6;           // partial buffers allocated for this many K splits
+  int ks;                // split-K factor of the projection GEMM (autotunable)
   int* status;
 };
 
@@ -738,7 +743,13 @@ las_status split_create(SplitState** out, int n, int X, int op, int Lc, const do
   s->status = status;
   {
     const long tiles = ((n + BM - 1) / BM) * ((op + BN - 1) / BN);
-    s->ksplit6 = (int)std::max(1L, std::min(64L, (2 * 148 + tiles - 1) / tiles));
+    s->ks = (int)std::max(1L, std::min(64L, (2 * 148 + tiles - 1) / tiles));
+    s->ksplit6 = 64;
+  }
+  // one-time launch attributes, so that later calls can be captured into CUDA graphs
+  if (ozaki_prepare() != LAS_OK || num_sms() <= 0) {
+    free(s);
+    return LAS_ERR_CUDA;
   }
   size_t total = 0;
   las_status rc = LAS_OK;
@@ -800,6 +811,9 @@ void split_destroy(SplitState* s) {
 
 const int* split_hexp(SplitState* s) { return s->Hexp; }
 
+int split_get_ksplit(SplitState* s) { return s->ks; }
+void split_set_ksplit(SplitState* s, int ks) { s->ks = std::max(1, std::min(ks, s->ksplit6)); }
+
 las_status split_prepare_C(SplitState* s, const double* Cocc, cudaStream_t st) {
   // rows p of C_occ^T (K = nu): element (p, nu) = Cocc[nu*op + p]
   RowsStrided acc{Cocc, 1, s->op, nullptr};
@@ -840,7 +854,7 @@ las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, i
   RowsStrided acc{Wt, R, 1, nullptr};
   las_status rc = slice_rows(acc, W, s->Wexp, st, s->mx);
   if (rc != LAS_OK) return rc;
-  const int ks = (int)std::max(1L, std::min((long)s->ksplit6, (R + 32 * 64 - 1) / (32 * 64)));
+  const int ks = (int)std::max(1L, std::min((long)s->ks, (R + 32 * 64 - 1) / (32 * 64)));
   rc = ozaki_gemm(s->HdigT, 0, nullptr, s->n, W, 0, s->Wexp, s->op, R, ks, 0, s->part, s->op,
                   (long)s->n * s->op, 0, 0, s->status, st);
   if (rc != LAS_OK) return rc;

@@ -21,13 +21,19 @@ PRECISIONS = {"fp64": LAS_FP64, "split": LAS_SPLIT_BF16, "split_bf16": LAS_SPLIT
 EXPORTS = ["las_create", "las_destroy", "las_set_stream", "las_sync", "las_device_bytes",
            "las_df_transform", "las_df_jk", "las_energy", "las_energy_grad",
            "las_energy_grad_host", "las_set_timing", "las_stage_times", "las_kernel_launches",
-           "las_split_gemm_workspace", "las_split_gemm", "las_status_str"]
+           "las_split_gemm_workspace", "las_split_gemm", "las_energy_grad_batched",
+           "las_autotune", "las_status_str"]
 
 
 class LasError(RuntimeError):
     def __init__(self, code: int, where: str, msg: str):
         super().__init__(f"{where}: status {code} ({msg})")
         self.code = code
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_void_p), ("h", ctypes.c_void_p), ("dm1s", ctypes.c_void_p),
+                ("dm2", ctypes.c_void_p), ("E", ctypes.c_void_p), ("dEdC", ctypes.c_void_p)]
 
 
 class _Dims(ctypes.Structure):
@@ -67,6 +73,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.las_split_gemm.argtypes = [ctypes.c_long] * 3 + [vp, ctypes.c_long, vp, ctypes.c_long,
                                                          vp, ctypes.c_long, vp, sz, vp]
     lib.las_split_gemm.restype = i
+    lib.las_energy_grad_batched.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(BatchItem), vp]
+    lib.las_energy_grad_batched.restype = i
+    lib.las_autotune.argtypes = [vp] * 7
+    lib.las_autotune.restype = i
     lib.las_kernel_launches.argtypes = []
     lib.las_kernel_launches.restype = ctypes.c_long
     lib.las_status_str.argtypes = [i]
@@ -191,6 +201,14 @@ class LasDF:
                "las_energy_grad_host")
         return float(E[0]), G
 
+    def autotune(self, C, h, dm1s, dm2):
+        """Pick the fastest split-K factor of the projection GEMM for this problem."""
+        import torch
+        E = torch.empty((), dtype=torch.float64, device=C.device)
+        G = torch.empty((self.nao, self.nmo), dtype=torch.float64, device=C.device)
+        _check(self._lib.las_autotune(self._h, _ptr(C), _ptr(h), _ptr(dm1s), _ptr(dm2),
+                                      _ptr(E), _ptr(G)), "las_autotune")
+
     def df_jk(self, C, J=None, K=None):
         import torch
         n = self.nao
@@ -210,6 +228,20 @@ class LasDF:
         _check(self._lib.las_df_transform(self._h, _ptr(C), p0, p1, _ptr(lmu), _ptr(lpu)),
                "las_df_transform")
         return lmu, lpu
+
+
+def energy_grad_batched(problems, items, stream=None):
+    """Evaluate many problems (LasDF objects) under one captured CUDA graph.
+
+    items: list of (C, h, dm1s, dm2, E, dEdC) device tensors, one tuple per problem; the same
+    tensors passed again replay the captured graph."""
+    import torch
+    lib = load_library()
+    n = len(problems)
+    arr = (ctypes.c_void_p * n)(*[p._h.value for p in problems])
+    its = (BatchItem * n)(*[BatchItem(*[_ptr(t) for t in it]) for it in items])
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(lib.las_energy_grad_batched(n, arr, its, st), "las_energy_grad_batched")
 
 
 def split_gemm(A, B, out=None, stream=None):
