@@ -42,6 +42,28 @@ def measured_peaks() -> dict:
         return {}
 
 
+def max_over_ranks(value: float, ws: int, device=None) -> float:
+    """The timed region's duration as the maximum over ranks (all_reduce MAX)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_rate(ws: int, steps: int, seconds: float) -> float:
+    """Whole-job evaluations per second: every rank evaluates its own system each step."""
+    return ws * steps / seconds
+
+
+def rank_seed(rank: int) -> int:
+    """Independent problems per rank: the Nao=1200 system drawn with a rank-specific seed."""
+    from las_inputs import BASE_SEED
+    return BASE_SEED + 2 + 1000 * rank
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -120,7 +142,7 @@ def make_inputs(rank: int):
     from las_inputs import BASE_SEED, make_system
     w = WORKLOAD
     t0 = time.time()
-    s = make_system(w["nao"], w["naux"], w["ncore"], w["frags"], seed=BASE_SEED + 2 + 1000 * rank)
+    s = make_system(w["nao"], w["naux"], w["ncore"], w["frags"], seed=rank_seed(rank))
     return s, time.time() - t0
 
 
@@ -181,11 +203,7 @@ def run_ours(args, ws, rank, local):
                 dist.barrier()
             ck = clocks.stop()
             las.set_timing(False)
-        ms = ev0.elapsed_time(ev1)
-        if ws > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
         E_val = float(E.item())
 
         # end to end through the host-buffer C-ABI call (H2D of the step's inputs, D2H of E and
@@ -201,16 +219,14 @@ def run_ours(args, ws, rank, local):
             for _ in range(steps):
                 e2e_E, _ = las.energy_grad_host(Ch, hh, d1h, d2h)
             t_e2e = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks(t_e2e, ws, dev)
         bi = Ch.nbytes + hh.nbytes + d1h.nbytes + d2h.nbytes
         bo = 8 + Gh.nbytes
         las.close()
         results[prec] = dict(ms_per_step=ms / steps, steps=steps, warmup=warm,
-                             evals_per_s=ws * steps / (ms / 1e3), stage_ms=stage_ms,
-                             E=E_val, e2e_evals_per_s=ws * steps / t_e2e, e2e_E=e2e_E,
+                             evals_per_s=weak_scaling_rate(ws, steps, ms / 1e3),
+                             stage_ms=stage_ms, E=E_val,
+                             e2e_evals_per_s=weak_scaling_rate(ws, steps, t_e2e), e2e_E=e2e_E,
                              h2d=bi, d2h=bo, clocks=ck, launches=launches)
     del Bd
     torch.cuda.empty_cache()
@@ -218,7 +234,10 @@ def run_ours(args, ws, rank, local):
 
 
 NDIG_PRODUCTS = 21     # digit products of the split-precision GEMM (6 digits, s + t <= 5)
-S1_TRAFFIC_PER_ROW = None   # dram bytes per (L, mu) row of the half transform, from ncu (profiles/)
+# DRAM bytes per (L, mu) row of the half-transform kernel (K = Nao = 1200, 192 columns), from one
+# ncu capture of the same kernel on 131072 rows (profiles/k_ozaki_m131072_k1200_n192.md), scaled
+# to a full launch by the rows it processes (the traffic is proportional to the rows).
+S1_TRAFFIC_PER_ROW = (1.937758e9 + 0.206009e9) / 131072
 
 
 def roofline_for(prec, r, work, peaks, s):
@@ -283,6 +302,34 @@ def _first_rows_B(seed, n, naux, rows):
     return out
 
 
+def split_gemm_probe(spec: str, steps: int, warmup: int):
+    """Time the emulated-FP64 GEMM C = A B (A: M x K, B: K x N, seeded Gaussians) on cuda:0."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2505_03755_gb300 import split_gemm
+    M, K, N = (int(v) for v in spec.split(","))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn(M, K, dtype=torch.float64, device="cuda", generator=g)
+    B = torch.randn(K, N, dtype=torch.float64, device="cuda", generator=g)
+    for _ in range(max(1, warmup)):
+        C = split_gemm(A, B)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        C = split_gemm(A, B)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ref = A[:64] @ B
+    err = float(((C[:64] - ref).abs().max() / ref.abs().max()).item())
+    print(json.dumps({"probe": "split_gemm", "M": M, "K": K, "N": N, "ms": ms,
+                      "digit_product_tflops": NDIG_PRODUCTS * 2.0 * M * K * N / ms / 1e9,
+                      "fp64_equiv_tflops": 2.0 * M * K * N / ms / 1e9,
+                      "max_rel_err_first_rows": err}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -294,7 +341,12 @@ def main():
     ap.add_argument("--fp64-warmup", type=int, default=3)
     ap.add_argument("--cpu-rows", type=int, default=240)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--split-gemm", default=None, metavar="M,K,N",
+                    help="time only the emulated-FP64 GEMM on random M x K and K x N inputs")
     args = ap.parse_args()
+    if args.split_gemm:
+        split_gemm_probe(args.split_gemm, args.steps, args.warmup)
+        return
     ws, rank, local = dist_env()
     if args.warmup < 3:
         args.warmup = 3

@@ -498,7 +498,9 @@ extern "C" las_status las_df_jk(las_ctx* x, const double* C, double* J, double* 
       launch_per_aux(x->T, nL, op, nullptr, nullptr, x->fi_c, x->W, x->eps + l0,
                      x->vc + l0, x->va + l0, 0, nullptr, x->status, x->stream);
     }
-    if (K) {  // K = 2 sum_{L,i} H_L(:,i) H_L(:,i)^T
+    if (K && x->prec == LAS_SPLIT_BF16) {  // K = 2 sum_{L,i} H_L(:,i) H_L(:,i)^T (x2 below)
+      if ((st = split_exchange(x->split, nL, x->Ht, K, l0 > 0, x->stream)) != LAS_OK) return st;
+    } else if (K) {  // K = 2 sum_{L,i} H_L(:,i) H_L(:,i)^T
       StridedA A{x->Ht, 0, 1, n};
       StridedA B{x->Ht, 0, n, 1};
       int ks = std::max(1, std::min(x->ksplit, (nL * op) / 64));
@@ -514,6 +516,7 @@ extern "C" las_status las_df_jk(las_ctx* x, const double* C, double* J, double* 
     }
     if ((st = check_launch()) != LAS_OK) return st;
   }
+  if (K && x->prec == LAS_SPLIT_BF16) launch_scale(K, (long)n * n, 2.0, x->stream);
   if (J) {
     launch_coulomb_packed(x->Bp, x->vc, x->X, x->npair, x->Jp, x->stream);
     launch_unpack_sym(x->Jp, n, J, x->stream);

@@ -83,6 +83,7 @@ las_status per_aux_prepare(int nact);
 void launch_per_aux(const double* T, int nL, int op, const double* dm1s, const double* dm2,
                     const FragInfo& fi, double* W, double* eps, double* vc, double* va,
                     int with_grad, const int* gexp, int* status, cudaStream_t s);
+void launch_scale(double* p, long count, double a, cudaStream_t s);
 void launch_reduce_partials(const double* part, int nsplit, long count, double* out,
                             int accumulate, cudaStream_t s);
 void launch_assemble_grad(const double* Out, const double* hC, const double* dm1s,

@@ -192,6 +192,11 @@ k_per_aux(const double* __restrict__ T, int nL, int op, const double* __restrict
   }
 }
 
+__global__ void k_scale(double* __restrict__ p, long count, double a) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < count) p[i] *= a;
+}
+
 __global__ void k_reduce_partials(const double* __restrict__ part, int nsplit, long count,
                                   double* __restrict__ out, int accumulate) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -327,6 +332,12 @@ void launch_per_aux(const double* T, int nL, int op, const double* dm1s, const d
   size_t smem = (3 * (size_t)fi.nact * fi.nact + 256 + LAS_MAX_FRAG) * sizeof(double);
   k_per_aux<<<nL, 256, smem, s>>>(T, nL, op, dm1s, dm2, fi, W, eps, vc, va, with_grad, gexp,
                                   status);
+  las_count_launch();
+}
+
+void launch_scale(double* p, long count, double a, cudaStream_t s) {
+  if (count <= 0) return;
+  k_scale<<<nblk(count, 256), 256, 0, s>>>(p, count, a);
   las_count_launch();
 }
 

@@ -478,7 +478,9 @@ k_digits_long(Acc acc, Planes P, const unsigned long long* mx, int* ex) {
   const long kend = P.nkb * BK;
   const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i >= P.Rpad * kend) return;
-  const long r = i / kend, k = i - r * kend;
+  // thread order follows the K-blocked output: (k block, row, k within the block)
+  const long kb = i / (P.Rpad * BK), rem = i - kb * (P.Rpad * BK);
+  const long r = rem / BK, k = kb * BK + (rem - r * BK);
   const bool live = r < P.R;
   const int e = live ? exp_of_maxbits(mx[r]) : 0;
   if (k == 0 && live) ex[r] = e;
@@ -708,7 +710,7 @@ struct SplitState {
   Planes Wdig;           // rows q, K = (L, p)
   int* Wexp;             // [op]
   double* part;          // [ksplit][n][op]
-  unsigned long long* mx;  // [op] row maxima for long-row slicing
+  unsigned long long* mx;  // [op + n] row maxima for long-row slicing
   Planes hdig;           // rows mu of h, K = nu
   int* hexp;             // [n]
   Planes hcdig;          // rows q of (h C_occ)^T, K = mu
@@ -775,7 +777,7 @@ las_status split_create(SplitState** out, int n, int X, int op, int Lc, const do
   A(&q, planes_bytes(op, R));        s->Wdig = make_planes(q, op, R);   q = nullptr;
   A((void**)&s->Wexp, (size_t)op * 4);
   A((void**)&s->part, (size_t)s->ksplit6 * n * op * 8);
-  A((void**)&s->mx, (size_t)op * 8);
+  A((void**)&s->mx, (size_t)(op + n) * 8);
   A(&q, planes_bytes(n, n));         s->hdig = make_planes(q, n, n);    q = nullptr;
   A((void**)&s->hexp, (size_t)n * 4);
   A(&q, planes_bytes(op, n));        s->hcdig = make_planes(q, op, n);  q = nullptr;
@@ -859,6 +861,27 @@ las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, i
                   (long)s->n * s->op, 0, 0, s->status, st);
   if (rc != LAS_OK) return rc;
   launch_reduce_partials(s->part, ks, (long)s->n * s->op, Out, accumulate, st);
+  return LAS_OK;
+}
+
+las_status split_exchange(SplitState* s, int nL, const double* Ht, double* K, int accumulate,
+                          cudaStream_t st) {
+  // K(mu,nu) (+)= sum_{(L,p)} Ht[(L,p)][mu] Ht[(L,p)][nu]: rows mu of H^T, scaled per row over
+  // the long index (L,p), serve as both operands
+  const long R = (long)nL * s->op, n = s->n;
+  Planes HT = s->HdigT;
+  HT.K = R;
+  las_status rc = slice_rows(RowsStrided{Ht, 1, n, nullptr}, HT, s->hexp, st, s->mx);
+  if (rc != LAS_OK) return rc;
+  // partials [ks][n][n] live in the projection's partial buffer (64 * n * op doubles)
+  const long cap = std::max(1L, (64L * s->op) / n);
+  const long tiles = ((n + BM - 1) / BM) * ((n + BN - 1) / BN);
+  const int ks = (int)std::max(1L, std::min(cap, std::min((2L * num_sms() + tiles - 1) / tiles,
+                                                          (R + 32 * 64 - 1) / (32 * 64))));
+  rc = ozaki_gemm(HT, 0, s->hexp, n, HT, 0, s->hexp, n, R, ks, 0, s->part, n, n * n, 0, 0,
+                  s->status, st);
+  if (rc != LAS_OK) return rc;
+  launch_reduce_partials(s->part, ks, n * n, K, accumulate, st);
   return LAS_OK;
 }
 

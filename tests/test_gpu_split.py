@@ -111,3 +111,15 @@ def test_config1_split():
     E, G, _ = gpu_energy_grad(s, "split", want_gorb=False)
     assert abs(E - ref["E"]) <= E_ABS
     assert np.abs(G - ref["G"]).max() <= G_ABS
+
+
+@pytest.mark.parametrize("name", ["ragged", "cfg0"])
+def test_split_df_jk(name):
+    s = SMALL[name]()
+    las = make_las(s, "split")
+    J, K = las.df_jk(dev(s.C))
+    las.sync()
+    ref = O.system_energy_grad(s, with_grad=False)
+    assert np.abs(J.cpu().numpy() - ref["J"]).max() <= 1e-11 * np.abs(ref["J"]).max()
+    assert np.abs(K.cpu().numpy() - ref["K"]).max() <= 1e-11 * np.abs(ref["K"]).max()
+    las.close()
