@@ -147,7 +147,8 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   uint64_t* accf = bars + 2 * NSTAGE;
   uint64_t* acce = bars + 2 * NSTAGE + 1;
   uint64_t* drain = bars + 2 * NSTAGE + 2;
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * NSTAGE + 3);
+  uint64_t* accT = bars + 2 * NSTAGE + 3;   // tail accumulator read out (once per tile)
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * NSTAGE + 4);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -160,6 +161,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     }
     sm100::mbar_init(accf, 1);
     sm100::mbar_init(acce, 8);
+    sm100::mbar_init(accT, 8);
     sm100::mbar_init(drain, 1);
     *abort_flag = 0;
     sm100::fence_mbar_init();
@@ -202,11 +204,25 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
                        LAS_ERR_TIMEOUT);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    long gs = 0, gc = 0;
-    bool ok = true;
-    for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    // Per stage the tail MMAs are issued at once; the exact-group MMAs of the first stages of a
+    // chunk may be deferred (their stages stay resident) until the epilogue has drained the
+    // previous chunk, so that the drain overlaps tensor work.
+    long gs = 0, gc = 0, tcount = 0;
+    bool ok = true, need_acce = false;
+    for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
       int m0, n0, kb0, nkb;
       tile_coords(p, t, m0, n0, kb0, nkb);
+      // the tail accumulator of the previous tile must have been read out
+      if (tcount > 0) {
+        if (!sm100::mbar_wait(accT, (uint32_t)(tcount - 1) & 1, abort_flag, p.status,
+                              LAS_ERR_TIMEOUT)) {
+          ok = false;
+          break;
+        }
+        sm100::tc_fence_after();
+      }
+      long pend0 = 0;     // first deferred stage (global index) and count
+      int npend = 0, pend_i0 = 0;
       for (int i = 0; i < nkb; ++i, ++gs) {
         const int st = (int)(gs % NSTAGE);
         if (!sm100::mbar_wait(&full[st], (uint32_t)(gs / NSTAGE) & 1, abort_flag, p.status,
@@ -215,49 +231,65 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
           break;
         }
         sm100::tc_fence_after();
-        const bool first_in_chunk = (i % CHUNK) == 0;
-        // a new tile reuses every accumulator: wait until the previous tile has been read out
-        if (i == 0 && gc > 0) {
+        {
+          const uint32_t sa = sm100::smem_u32(smem + st * STAGE_BYTES);
+          const uint32_t sb = sa + A_BYTES;
+          bool tail_acc = (i > 0);
+          for (int s = 0; s < NDIG; ++s)
+            for (int t2 = (s >= NEXACT ? 0 : NEXACT - s); s + t2 <= NDIG - 1; ++t2) {
+              sm100::mma_bf16(tmem + COL_TAIL, sm100::smem_desc_sw32(sa + s * A_PLANE),
+                              sm100::smem_desc_sw32(sb + t2 * B_PLANE), IDESC,
+                              tail_acc ? 1u : 0u);
+              tail_acc = true;
+            }
+        }
+        const bool last_in_chunk = (i % CHUNK) == CHUNK - 1 || i == nkb - 1;
+        if (need_acce) {
+          if (!last_in_chunk && npend < NSTAGE - 1 &&
+              !sm100::mbar_try_wait(acce, (uint32_t)(gc - 1) & 1)) {
+            if (npend == 0) {
+              pend0 = gs;
+              pend_i0 = i;
+            }
+            ++npend;
+            continue;   // defer this stage's exact-group MMAs
+          }
           if (!sm100::mbar_wait(acce, (uint32_t)(gc - 1) & 1, abort_flag, p.status,
                                 LAS_ERR_TIMEOUT)) {
             ok = false;
             break;
           }
           sm100::tc_fence_after();
+          need_acce = false;
         }
-        const uint32_t sa = sm100::smem_u32(smem + st * STAGE_BYTES);
-        const uint32_t sb = sa + A_BYTES;
-        // tail weights q = 4, 5 into one FP32 accumulator
-        bool tail_acc = (i > 0);
-        for (int s = 0; s < NDIG; ++s)
-          for (int t2 = (s >= NEXACT ? 0 : NEXACT - s); s + t2 <= NDIG - 1; ++t2) {
-            sm100::mma_bf16(tmem + COL_TAIL, sm100::smem_desc_sw32(sa + s * A_PLANE),
-                            sm100::smem_desc_sw32(sb + t2 * B_PLANE), IDESC, tail_acc ? 1u : 0u);
-            tail_acc = true;
-          }
-        // a later chunk of the same tile: its exact accumulators must have been drained
-        if (first_in_chunk && i > 0) {
-          if (!sm100::mbar_wait(acce, (uint32_t)(gc - 1) & 1, abort_flag, p.status,
-                                LAS_ERR_TIMEOUT)) {
-            ok = false;
-            break;
-          }
-          sm100::tc_fence_after();
+        if (npend == 0) {
+          pend0 = gs;
+          pend_i0 = i;
         }
-        // exact weights q = 0..3
-        for (int q = 0; q < NEXACT; ++q) {
-          bool started = !first_in_chunk;
-          for (int s = 0; s <= q; ++s) {
-            sm100::mma_bf16(tmem + COL_EXACT0 + q * BN, sm100::smem_desc_sw32(sa + s * A_PLANE),
-                            sm100::smem_desc_sw32(sb + (q - s) * B_PLANE), IDESC,
-                            started ? 1u : 0u);
-            started = true;
+        // exact weights q = 0..3 for the deferred stages and this one, in stage order
+        for (int j = 0; j <= npend; ++j) {
+          const long g2 = pend0 + j;
+          const int i2 = pend_i0 + j;
+          const int st2 = (int)(g2 % NSTAGE);
+          const bool first_in_chunk = (i2 % CHUNK) == 0;
+          const uint32_t sa = sm100::smem_u32(smem + st2 * STAGE_BYTES);
+          const uint32_t sb = sa + A_BYTES;
+          for (int q = 0; q < NEXACT; ++q) {
+            bool started = !first_in_chunk;
+            for (int s = 0; s <= q; ++s) {
+              sm100::mma_bf16(tmem + COL_EXACT0 + q * BN, sm100::smem_desc_sw32(sa + s * A_PLANE),
+                              sm100::smem_desc_sw32(sb + (q - s) * B_PLANE), IDESC,
+                              started ? 1u : 0u);
+              started = true;
+            }
           }
+          sm100::mma_commit(&empty[st2]);
         }
-        sm100::mma_commit(&empty[st]);
-        if ((i % CHUNK) == CHUNK - 1 || i == nkb - 1) {
+        npend = 0;
+        if (last_in_chunk) {
           sm100::mma_commit(accf);
           ++gc;
+          need_acce = true;   // the next chunk's exact MMAs wait for this chunk's drain
         }
       }
     }
@@ -276,18 +308,40 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
       int m0, n0, kb0, nkb;
       tile_coords(p, t, m0, n0, kb0, nkb);
       const int nchunks = (nkb + CHUNK - 1) / CHUNK;
-      long long acc[48];
+      unsigned long long acc[48];
 #pragma unroll
       for (int j = 0; j < 48; ++j) acc[j] = 0;
       for (int c = 0; c < nchunks; ++c, ++gc) {
-        if (!sm100::mbar_wait(accf, (uint32_t)gc & 1, abort_flag, p.status, LAS_ERR_TIMEOUT)) {
+        if (!sm100::mbar_wait(accf, (uint32_t)gc & 1, abort_flag, p.status, LAS_ERR_TIMEOUT,
+                              256)) {
           ok = false;
           break;
         }
         sm100::tc_fence_after();
+        const bool fin = (c == nchunks - 1);
+        int extra = 0;
+        if (fin) {
+          // tail first, so that the next tile's tail MMAs can start:
+          // acc <- acc * 2^sh + rint(tail * 2^(24+sh))  (int64, modulo 2^64)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            uint32_t r[16];
+            sm100::tmem_ld16(tl + COL_TAIL + j * 16, r);
+            sm100::tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              acc[j * 16 + e] = (acc[j * 16 + e] << p.sh) +
+                                (unsigned long long)__float2ll_rn(__uint_as_float(r[e]) * tscale);
+          }
+          sm100::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) sm100::mbar_arrive(accT);
+          extra = p.sh;
+        }
 #pragma unroll
         for (int q = 0; q < NEXACT; ++q) {
           const float up = __int_as_float((127 + 8 * q) << 23);   // 2^(8q)
+          const int shq = 8 * (NEXACT - 1 - q) + extra;
 #pragma unroll
           for (int j = 0; j < 3; ++j) {
             uint32_t r[16];
@@ -296,26 +350,13 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
               const int iv = __float2int_rn(__uint_as_float(r[e]) * up);
-              acc[j * 16 + e] += (long long)iv * (1ll << (8 * (NEXACT - 1 - q)));
+              acc[j * 16 + e] += (unsigned long long)(long long)iv << shq;
             }
-          }
-        }
-        if (c == nchunks - 1) {
-          // merge the FP32 tail: acc <- acc * 2^sh + rint(tail * 2^(24+sh))
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            uint32_t r[16];
-            sm100::tmem_ld16(tl + COL_TAIL + j * 16, r);
-            sm100::tmem_wait_ld();
-#pragma unroll
-            for (int e = 0; e < 16; ++e)
-              acc[j * 16 + e] = (long long)((unsigned long long)acc[j * 16 + e] << p.sh) +
-                                __float2ll_rn(__uint_as_float(r[e]) * tscale);
           }
         }
         sm100::tc_fence_before();
         __syncwarp();
-        if (lane == 0) sm100::mbar_arrive(acce);   // TMEM may be overwritten from here on
+        if (lane == 0) sm100::mbar_arrive(acce);   // exact accumulators free from here on
       }
       if (!ok) break;
       // FP64 results (overlaps the next tile's MMAs)
@@ -332,7 +373,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
         const int col = n0 + half * 48 + j;
         if (row < p.M && col < p.N) {
           const int E = ea + p.eb[col] - 14 - 8 * (NEXACT - 1) - p.sh;
-          const double v = make_double(acc[j], E);
+          const double v = make_double((long long)acc[j], E);
           if (p.mode == 0)
             p.out[(long)z * p.zstride + (long)row * p.ldc + col] = v;
           else
@@ -387,21 +428,33 @@ __device__ __forceinline__ void digits_of(double xv, int e, __nv_bfloat16 (&out)
   unsigned long long m = b & 0xFFFFFFFFFFFFFull;
   int ee = bex;
   if (bex != 0) m |= (1ull << 52); else ee = 1;
-  // |x| * 2^(47 - e) = m * 2^(ee - 1075 + 47 - e)
+  // |x| * 2^(47 - e) = m * 2^(ee - 1075 + 47 - e), rounded to an integer below 2^47
   const int shift = ee - 1028 - e;
   unsigned long long y;
   if (shift >= 0) y = m << shift;
   else if (shift > -63) y = (m + (1ull << (-shift - 1))) >> (-shift);
   else y = 0;
-  long long Y = (b >> 63) ? -(long long)y : (long long)y;
+  // balanced base-256 digits from the bottom, in 32-bit arithmetic on two 24-bit halves
+  int lo = (int)(y & 0xFFFFFF), hi = (int)(y >> 24);
+  if (b >> 63) {
+    lo = -lo;
+    hi = -hi;
+  }
   int d[NDIG];
 #pragma unroll
-  for (int s = NDIG - 1; s >= 1; --s) {
-    const long long t = ((Y + 128) & 255) - 128;
-    d[s] = (int)t;
-    Y = (Y - t) >> 8;
+  for (int s = NDIG - 1; s >= 3; --s) {
+    const int t = ((lo + 128) & 255) - 128;
+    d[s] = t;
+    lo = (lo - t) >> 8;
   }
-  d[0] = (int)Y;
+  hi += lo;   // carry out of the low half (-1, 0 or 1)
+#pragma unroll
+  for (int s = 2; s >= 1; --s) {
+    const int t = ((hi + 128) & 255) - 128;
+    d[s] = t;
+    hi = (hi - t) >> 8;
+  }
+  d[0] = hi;
 #pragma unroll
   for (int s = 0; s < NDIG; ++s)
     out[s] = __float2bfloat16_rn((float)d[s] * __int_as_float((127 - 8 * s) << 23));

@@ -49,11 +49,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait on phase `parity`.  Returns false (and raises the abort flag) on timeout or when
-// another role already aborted.
+// another role already aborted.  sleep_ns > 0 backs off between polls (for waiters whose latency
+// does not matter, so that they leave issue slots to the latency-critical warps).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
-                                          int* status, int code) {
+                                          int* status, int code, unsigned sleep_ns = 0) {
   for (long it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (sleep_ns) __nanosleep(sleep_ns);
     if ((it & 1023) == 1023) {
       if (*abort) return false;
       if (it > (1L << 24)) {  // ~seconds: far beyond any legitimate wait
@@ -107,6 +109,23 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+
+// D[tmem] (+)= A[tmem] * B[smem desc]^T, kind::f16; A holds 128 rows (lanes) x 16 BF16 in 8
+// consecutive 32-bit columns.
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Copy a 128-row x 256-bit tile (128 x 16 BF16) from shared memory (matrix descriptor) into 8
+// TMEM columns starting at taddr.
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc) {
+  asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
 }
 
 // Arrive on `bar` once every previously issued tcgen05.mma of this thread has completed.
