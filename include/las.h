@@ -97,6 +97,16 @@ las_status las_df_transform(las_ctx* ctx, const double* C, int p0, int p1, doubl
  * J, K: device [nao][nao]; either may be NULL. */
 las_status las_df_jk(las_ctx* ctx, const double* C, double* J, double* K);
 
+/* The JK call of Eqs. J_1-K_2 for a general symmetric density given in factored form,
+ *   D = sum_{k < r} w[k] Cx[:,k] Cx[:,k]^T     (Cx: device [nao][r] row-major, w: device [r]),
+ * e.g. D = C_x M C_x^T after diagonalising M, or one spin density gamma_sigma of Eq. v_emb:
+ *   J[mu][nu] = sum_L b^L_{mu nu} Tr(b^L D),   K[mu][nu] = sum_L (b^L D b^L)_{mu nu}.
+ * Weights of either sign are allowed (D = D+ - D- is evaluated as two factored parts).
+ * Requires r <= ncore + sum(nact) of the context (create a JK context with ncore >= r and no
+ * fragments for densities of other ranks).  J, K: device [nao][nao]; either may be NULL. */
+las_status las_df_jk_density(las_ctx* ctx, const double* Cx, const double* w, int r, double* J,
+                             double* K);
+
 /* LAS energy.  h: device [nao][nao] one-electron Hamiltonian (symmetric).
  * dm1s: device, per fragment K the spin-separated 1-RDM [2][m_K][m_K] (alpha, beta),
  *       concatenated over fragments.

@@ -63,6 +63,8 @@ struct las_ctx {
   double* vc;     // [X]
   double* va;     // [X]
   double* Jp;     // [npair] (JK)
+  double* Jt;     // [n][n]  J of one sign part (general-density JK)
+  double* Kt;     // [n][n]  K of one sign part
   int* status;    // device status word
   // staging for the host-buffer call
   double *dC, *dh, *ddm1, *ddm2, *dE, *dG;
@@ -105,7 +107,8 @@ static las_status dalloc(las_ctx* x, void** p, size_t bytes) {
 
 static void free_all(las_ctx* x) {
   void* ptrs[] = {x->Cocc, x->Ht, x->T, x->W, x->part, x->Out, x->hC, x->hmo, x->M, x->eps,
-                  x->vc, x->va, x->Jp, x->status, x->dC, x->dh, x->ddm1, x->ddm2, x->dE, x->dG};
+                  x->vc, x->va, x->Jp, x->Jt, x->Kt, x->status, x->dC, x->dh, x->ddm1, x->ddm2,
+                  x->dE, x->dG};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (x->split) split_destroy(x->split);
@@ -204,6 +207,8 @@ extern "C" las_status las_create(las_ctx** out, const las_dims* d, const double*
   ALLOC(vc, x->X);
   ALLOC(va, x->X);
   ALLOC(Jp, x->npair);
+  ALLOC(Jt, (size_t)x->n * x->n);
+  ALLOC(Kt, (size_t)x->n * x->n);
   ALLOC(status, 4);
   ALLOC(dC, (size_t)x->n * x->nmo);
   ALLOC(dh, (size_t)x->n * x->n);
@@ -475,6 +480,53 @@ extern "C" las_status las_energy_grad_host(las_ctx* x, const double* C_host,
   return las_sync(x);
 }
 
+// J and K of the density D = sum_{k < r} c_k c_k^T whose columns c_k are in x->Cocc (columns >= r
+// zero):  J[mu][nu] = sum_L b^L_{mu nu} Tr(b^L D)  (Eqs. J_1, J_2),
+//         K[mu][nu] = sum_L (b^L D b^L)_{mu nu}   (Eqs. K_1, K_2, with b^L D = H_L C^T).
+static las_status jk_raw(las_ctx* x, int r, double* J, double* K) {
+  const int n = x->n, op = x->op;
+  FragInfo fr;
+  memset(&fr, 0, sizeof(fr));
+  fr.ncore = r;
+  if (x->prec == LAS_SPLIT_BF16) {
+    las_status st = split_prepare_C(x->split, x->Cocc, x->stream);
+    if (st != LAS_OK) return st;
+  }
+  las_status st;
+  for (int l0 = 0; l0 < x->X; l0 += x->Lc) {
+    const int nL = std::min(x->Lc, x->X - l0);
+    if ((st = half_and_full(x, l0, nL, J != nullptr)) != LAS_OK) return st;
+    if (J) {  // vc_L = 2 sum_k T_L(k,k) = 2 Tr(b^L D)
+      launch_per_aux(x->T, nL, op, nullptr, nullptr, fr, x->W, x->eps + l0, x->vc + l0,
+                     x->va + l0, 0, nullptr, x->status, x->stream);
+    }
+    if (K && x->prec == LAS_SPLIT_BF16) {  // K = sum_{L,k} H_L(:,k) H_L(:,k)^T
+      if ((st = split_exchange(x->split, nL, x->Ht, K, l0 > 0, x->stream)) != LAS_OK) return st;
+    } else if (K) {
+      StridedA A{x->Ht, 0, 1, n};
+      StridedA B{x->Ht, 0, n, 1};
+      int ks = std::max(1, std::min(x->ksplit, (nL * op) / 64));
+      // reuse `part` as [ks][n][n] only when it is large enough; otherwise accumulate directly
+      if ((size_t)ks * n * n <= (size_t)x->ksplit * n * op) {
+        StridedC Pk{x->part, (long)n * n, n, 1, 1.0, 0};
+        gemm_f64(n, n, nL * op, 1, ks, A, B, Pk, x->stream);
+        launch_reduce_partials(x->part, ks, (long)n * n, K, l0 > 0, x->stream);
+      } else {
+        StridedC Kd{K, 0, n, 1, 1.0, l0 > 0};
+        gemm_f64(n, n, nL * op, 1, 1, A, B, Kd, x->stream);
+      }
+    }
+    if ((st = check_launch()) != LAS_OK) return st;
+  }
+  if (K && x->prec == LAS_SPLIT_BF16) launch_mirror_lower(K, n, x->stream);
+  if (J) {
+    launch_coulomb_packed(x->Bp, x->vc, x->X, x->npair, x->Jp, x->stream);
+    launch_unpack_sym(x->Jp, n, J, x->stream);
+    launch_scale(J, (long)n * n, 0.5, x->stream);   // vc carried the factor 2
+  }
+  return check_launch();
+}
+
 extern "C" las_status las_df_jk(las_ctx* x, const double* C, double* J, double* K) {
   if (!x || !C) return LAS_ERR_ARG;
   if (!J && !K) return LAS_OK;
@@ -484,43 +536,35 @@ extern "C" las_status las_df_jk(las_ctx* x, const double* C, double* J, double* 
     if (K) LAS_CUDA_TRY(cudaMemsetAsync(K, 0, (size_t)n * n * 8, x->stream));
     return LAS_OK;
   }
-  // core-only C_occ (columns >= c zeroed) so that H holds b^L C_core
+  // core-only C_occ (columns >= c zeroed): D = C_core C_core^T and Dc = 2 D
   launch_pack_cocc(C, n, x->nmo, c, op, x->Cocc, x->stream);
-  if (x->prec == LAS_SPLIT_BF16) {
-    las_status st = split_prepare_C(x->split, x->Cocc, x->stream);
-    if (st != LAS_OK) return st;
+  las_status st = jk_raw(x, c, J, K);
+  if (st != LAS_OK) return st;
+  if (J) launch_scale(J, (long)n * n, 2.0, x->stream);
+  if (K) launch_scale(K, (long)n * n, 2.0, x->stream);
+  return check_launch();
+}
+
+extern "C" las_status las_df_jk_density(las_ctx* x, const double* Cx, const double* w, int r,
+                                        double* J, double* K) {
+  if (!x || !Cx || !w || r < 0) return LAS_ERR_ARG;
+  if (r > x->o) return LAS_ERR_ARG;
+  if (!J && !K) return LAS_OK;
+  const int n = x->n;
+  if (r == 0) {
+    if (J) LAS_CUDA_TRY(cudaMemsetAsync(J, 0, (size_t)n * n * 8, x->stream));
+    if (K) LAS_CUDA_TRY(cudaMemsetAsync(K, 0, (size_t)n * n * 8, x->stream));
+    return LAS_OK;
   }
-  las_status st;
-  for (int l0 = 0; l0 < x->X; l0 += x->Lc) {
-    const int nL = std::min(x->Lc, x->X - l0);
-    if ((st = half_and_full(x, l0, nL, J != nullptr)) != LAS_OK) return st;
-    if (J) {  // vc_L = 2 sum_i T_L(i,i)
-      launch_per_aux(x->T, nL, op, nullptr, nullptr, x->fi_c, x->W, x->eps + l0,
-                     x->vc + l0, x->va + l0, 0, nullptr, x->status, x->stream);
-    }
-    if (K && x->prec == LAS_SPLIT_BF16) {  // K = 2 sum_{L,i} H_L(:,i) H_L(:,i)^T (x2 below)
-      if ((st = split_exchange(x->split, nL, x->Ht, K, l0 > 0, x->stream)) != LAS_OK) return st;
-    } else if (K) {  // K = 2 sum_{L,i} H_L(:,i) H_L(:,i)^T
-      StridedA A{x->Ht, 0, 1, n};
-      StridedA B{x->Ht, 0, n, 1};
-      int ks = std::max(1, std::min(x->ksplit, (nL * op) / 64));
-      // reuse `part` as [ks][n][n] only when it is large enough; otherwise accumulate directly
-      if ((size_t)ks * n * n <= (size_t)x->ksplit * n * op) {
-        StridedC Pk{x->part, (long)n * n, n, 1, 2.0, 0};
-        gemm_f64(n, n, nL * op, 1, ks, A, B, Pk, x->stream);
-        launch_reduce_partials(x->part, ks, (long)n * n, K, l0 > 0, x->stream);
-      } else {
-        StridedC Kd{K, 0, n, 1, 2.0, l0 > 0};
-        gemm_f64(n, n, nL * op, 1, 1, A, B, Kd, x->stream);
-      }
-    }
-    if ((st = check_launch()) != LAS_OK) return st;
-  }
-  if (K && x->prec == LAS_SPLIT_BF16) launch_scale(K, (long)n * n, 2.0, x->stream);
-  if (J) {
-    launch_coulomb_packed(x->Bp, x->vc, x->X, x->npair, x->Jp, x->stream);
-    launch_unpack_sym(x->Jp, n, J, x->stream);
-  }
+  // D = D+ - D-,  D± = sum_k max(±w_k, 0) c_k c_k^T
+  launch_pack_weighted(Cx, w, +1.0, n, r, x->op, x->Cocc, x->stream);
+  las_status st = jk_raw(x, r, J, K);
+  if (st != LAS_OK) return st;
+  launch_pack_weighted(Cx, w, -1.0, n, r, x->op, x->Cocc, x->stream);
+  st = jk_raw(x, r, J ? x->Jt : nullptr, K ? x->Kt : nullptr);
+  if (st != LAS_OK) return st;
+  if (J) launch_axpy(J, x->Jt, -1.0, (long)n * n, x->stream);
+  if (K) launch_axpy(K, x->Kt, -1.0, (long)n * n, x->stream);
   return check_launch();
 }
 

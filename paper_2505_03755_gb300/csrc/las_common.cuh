@@ -84,6 +84,10 @@ void launch_per_aux(const double* T, int nL, int op, const double* dm1s, const d
                     const FragInfo& fi, double* W, double* eps, double* vc, double* va,
                     int with_grad, const int* gexp, int* status, cudaStream_t s);
 void launch_scale(double* p, long count, double a, cudaStream_t s);
+void launch_mirror_lower(double* K, int n, cudaStream_t s);
+void launch_axpy(double* y, const double* x, double a, long count, cudaStream_t s);
+void launch_pack_weighted(const double* Cx, const double* w, double sign, int n, int r, int op,
+                          double* Cocc, cudaStream_t s);
 void launch_reduce_partials(const double* part, int nsplit, long count, double* out,
                             int accumulate, cudaStream_t s);
 void launch_assemble_grad(const double* Out, const double* hC, const double* dm1s,

@@ -192,6 +192,33 @@ k_per_aux(const double* __restrict__ T, int nL, int op, const double* __restrict
   }
 }
 
+// Cocc[mu][k] = Cx[mu][k] * sqrt(max(sign * w[k], 0)) for k < r, zero for r <= k < op
+__global__ void k_pack_weighted(const double* __restrict__ Cx, const double* __restrict__ w,
+                                double sign, int n, int r, int op, double* __restrict__ Cocc) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= (long)n * op) return;
+  const int mu = (int)(i / op), k = (int)(i % op);
+  double v = 0.0;
+  if (k < r) {
+    const double wk = sign * w[k];
+    if (wk > 0.0) v = Cx[(long)mu * r + k] * sqrt(wk);
+  }
+  Cocc[i] = v;
+}
+
+// K[i][j] = K[j][i] for i < j (copy the lower triangle to the upper)
+__global__ void k_mirror_lower(double* __restrict__ K, int n) {
+  long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  if (i < j) K[idx] = K[(long)j * n + i];
+}
+
+__global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, double a, long count) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < count) y[i] += a * x[i];
+}
+
 __global__ void k_scale(double* __restrict__ p, long count, double a) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i < count) p[i] *= a;
@@ -332,6 +359,23 @@ void launch_per_aux(const double* T, int nL, int op, const double* dm1s, const d
   size_t smem = (3 * (size_t)fi.nact * fi.nact + 256 + LAS_MAX_FRAG) * sizeof(double);
   k_per_aux<<<nL, 256, smem, s>>>(T, nL, op, dm1s, dm2, fi, W, eps, vc, va, with_grad, gexp,
                                   status);
+  las_count_launch();
+}
+
+void launch_pack_weighted(const double* Cx, const double* w, double sign, int n, int r, int op,
+                          double* Cocc, cudaStream_t s) {
+  k_pack_weighted<<<nblk((long)n * op, 256), 256, 0, s>>>(Cx, w, sign, n, r, op, Cocc);
+  las_count_launch();
+}
+
+void launch_mirror_lower(double* K, int n, cudaStream_t s) {
+  k_mirror_lower<<<nblk((long)n * n, 256), 256, 0, s>>>(K, n);
+  las_count_launch();
+}
+
+void launch_axpy(double* y, const double* x, double a, long count, cudaStream_t s) {
+  if (count <= 0) return;
+  k_axpy<<<nblk(count, 256), 256, 0, s>>>(y, x, a, count);
   las_count_launch();
 }
 

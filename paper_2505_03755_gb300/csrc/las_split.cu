@@ -88,6 +88,7 @@ struct OzParams {
   int mode;                // 0: out[z*zstride + r*ldc + c]; 1: Ht layout (rows (L,mu))
   long ldc, zstride;
   int ht_n, ht_op;
+  int lower;               // symmetric product: only tiles that touch the lower triangle
   int sh;                  // fractional bits kept when merging the tail
   int* status;
 };
@@ -184,6 +185,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int m0, n0, kb0, nkb;
       tile_coords(p, t, m0, n0, kb0, nkb);
+      if (p.lower && n0 >= m0 + BM) continue;
       for (int i = 0; i < nkb; ++i, ++gs) {
         const int st = (int)(gs % NSTAGE);
         if (gs >= NSTAGE && !sm100::mbar_wait(&empty[st], (uint32_t)((gs / NSTAGE) - 1) & 1,
@@ -209,9 +211,10 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     // previous chunk, so that the drain overlaps tensor work.
     long gs = 0, gc = 0, tcount = 0;
     bool ok = true, need_acce = false;
-    for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
+    for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int m0, n0, kb0, nkb;
       tile_coords(p, t, m0, n0, kb0, nkb);
+      if (p.lower && n0 >= m0 + BM) continue;
       // the tail accumulator of the previous tile must have been read out
       if (tcount > 0) {
         if (!sm100::mbar_wait(accT, (uint32_t)(tcount - 1) & 1, abort_flag, p.status,
@@ -292,6 +295,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
           need_acce = true;   // the next chunk's exact MMAs wait for this chunk's drain
         }
       }
+      ++tcount;
     }
     // make sure no MMA is still writing TMEM when the CTA tears down
     sm100::mma_commit(drain);
@@ -307,6 +311,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int m0, n0, kb0, nkb;
       tile_coords(p, t, m0, n0, kb0, nkb);
+      if (p.lower && n0 >= m0 + BM) continue;
       const int nchunks = (nkb + CHUNK - 1) / CHUNK;
       unsigned long long acc[48];
 #pragma unroll
@@ -673,7 +678,7 @@ static int num_sms() {
 las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const Planes& B,
                       long b_row0, const int* eb, long N, long K, int ksplit, int mode,
                       double* out, long ldc, long zstride, int ht_n, int ht_op, int* status,
-                      cudaStream_t st) {
+                      cudaStream_t st, int lower = 0) {
   if (M <= 0 || N <= 0) return LAS_OK;
   if (a_row0 + M > A.Rpad || b_row0 + N > B.Rpad || K > A.nkb * BK || K > B.nkb * BK)
     return LAS_ERR_INTERNAL;
@@ -703,6 +708,7 @@ las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const
   p.zstride = zstride;
   p.ht_n = ht_n;
   p.ht_op = ht_op;
+  p.lower = lower;
   // fractional bits kept for the tail: |fixed-point sum| < 2^38 * (k per CTA) must fit 62 bits
   int lgk = 0;
   while ((1L << lgk) < (long)p.kb_per_split * BK) ++lgk;
@@ -931,8 +937,9 @@ las_status split_exchange(SplitState* s, int nL, const double* Ht, double* K, in
   const long tiles = ((n + BM - 1) / BM) * ((n + BN - 1) / BN);
   const int ks = (int)std::max(1L, std::min(cap, std::min((2L * num_sms() + tiles - 1) / tiles,
                                                           (R + 32 * 64 - 1) / (32 * 64))));
+  // symmetric product: only tiles touching the lower triangle; the caller mirrors the result
   rc = ozaki_gemm(HT, 0, s->hexp, n, HT, 0, s->hexp, n, R, ks, 0, s->part, n, n * n, 0, 0,
-                  s->status, st);
+                  s->status, st, 1);
   if (rc != LAS_OK) return rc;
   launch_reduce_partials(s->part, ks, n * n, K, accumulate, st);
   return LAS_OK;

@@ -19,7 +19,8 @@ las_status split_prepare_C(SplitState* s, const double* Cocc, cudaStream_t st);
 las_status split_half(SplitState* s, int l0, int nL, double* Ht, cudaStream_t st);
 // S2: T[b] = Ht[b] C_occ   (op x op per b)
 las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaStream_t st);
-// K (+)= sum_{(L,p)} H(mu,(L,p)) H(nu,(L,p)) over the chunk's half transform Ht[(L,p)][mu]
+// K (+)= sum_{(L,p)} H(mu,(L,p)) H(nu,(L,p)) over the chunk's half transform Ht[(L,p)][mu];
+// only the lower triangle (mu >= nu) is valid: mirror it afterwards
 las_status split_exchange(SplitState* s, int nL, const double* Ht, double* K, int accumulate,
                           cudaStream_t st);
 // split-K factor of the projection GEMM (1..64)

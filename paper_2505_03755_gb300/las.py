@@ -22,7 +22,7 @@ EXPORTS = ["las_create", "las_destroy", "las_set_stream", "las_sync", "las_devic
            "las_df_transform", "las_df_jk", "las_energy", "las_energy_grad",
            "las_energy_grad_host", "las_set_timing", "las_stage_times", "las_kernel_launches",
            "las_split_gemm_workspace", "las_split_gemm", "las_energy_grad_batched",
-           "las_autotune", "las_status_str"]
+           "las_autotune", "las_df_jk_density", "las_status_str"]
 
 
 class LasError(RuntimeError):
@@ -77,6 +77,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.las_energy_grad_batched.restype = i
     lib.las_autotune.argtypes = [vp] * 7
     lib.las_autotune.restype = i
+    lib.las_df_jk_density.argtypes = [vp, vp, vp, i, vp, vp]
+    lib.las_df_jk_density.restype = i
     lib.las_kernel_launches.argtypes = []
     lib.las_kernel_launches.restype = ctypes.c_long
     lib.las_status_str.argtypes = [i]
@@ -215,6 +217,16 @@ class LasDF:
         J = torch.empty((n, n), dtype=torch.float64, device=C.device) if J is None else J
         K = torch.empty((n, n), dtype=torch.float64, device=C.device) if K is None else K
         _check(self._lib.las_df_jk(self._h, _ptr(C), _ptr(J), _ptr(K)), "las_df_jk")
+        return J, K
+
+    def df_jk_density(self, Cx, w, J=None, K=None):
+        """J and K of D = Cx diag(w) Cx^T (Cx: n x r, w: r; device float64 tensors)."""
+        import torch
+        n = self.nao
+        J = torch.empty((n, n), dtype=torch.float64, device=Cx.device) if J is None else J
+        K = torch.empty((n, n), dtype=torch.float64, device=Cx.device) if K is None else K
+        _check(self._lib.las_df_jk_density(self._h, _ptr(Cx), _ptr(w), int(Cx.shape[1]),
+                                           _ptr(J), _ptr(K)), "las_df_jk_density")
         return J, K
 
     def df_transform(self, C, p0: int, p1: int, want_lmu: bool = True, want_lpu: bool = True):

@@ -1,0 +1,59 @@
+"""The general-density JK call (Eqs. J_1-K_2) through las_df_jk_density, against the oracle's
+JK of the explicit density D = Cx diag(w) Cx^T (mixed-sign weights), in both precisions."""
+import numpy as np
+import pytest
+
+from gpu_common import built, dev, torch_cuda
+from las_inputs import make_system
+from oracle import las_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("split", 1e-11)])
+@pytest.mark.parametrize("r", [1, 12, 30])
+def test_df_jk_density(precision, tol, r):
+    torch_cuda()
+    built()
+    from paper_2505_03755_gb300 import LasDF
+    s = make_system(37, 53, 30, [], seed=606)      # a JK context: ncore >= r, no fragments
+    rng = np.random.default_rng(r)
+    Cx = rng.standard_normal((s.nao, r))
+    w = rng.standard_normal(r)
+    D = Cx @ np.diag(w) @ Cx.T
+    (Jr,), (Kr,) = O.df_jk(s.Bp, s.nao, [D])
+    las = LasDF(dev(s.Bp), s.nao, s.naux, s.nmo, s.ncore, [], precision=precision)
+    J, K = las.df_jk_density(dev(Cx), dev(w))
+    las.sync()
+    assert np.abs(J.cpu().numpy() - Jr).max() <= tol * np.abs(Jr).max()
+    assert np.abs(K.cpu().numpy() - Kr).max() <= tol * np.abs(Kr).max()
+    las.close()
+
+
+def test_df_jk_density_spin_densities_of_a_las_state():
+    """gamma_sigma = C_c C_c^T + C_a gamma^act_sigma C_a^T: the per-spin K of Eq. v_emb,
+    with the active block diagonalised on the host to give the factored form."""
+    torch_cuda()
+    built()
+    from paper_2505_03755_gb300 import LasDF
+    s = make_system(40, 70, 4, [(2, 2), (3, 3)], seed=77)
+    Dact, _ = O.active_rdms(s.dm1s, s.dm2)
+    c, a = s.ncore, s.nactive
+    for sigma in range(2):
+        g = np.zeros((a, a))
+        off = 0
+        for d in s.dm1s:
+            m = d.shape[-1]
+            g[off:off + m, off:off + m] = d[sigma]
+            off += m
+        lam, U = np.linalg.eigh(g)
+        Cx = np.concatenate([s.C[:, :c], s.C[:, c:c + a] @ U], axis=1)
+        w = np.concatenate([np.ones(c), lam])
+        D = s.C[:, :c] @ s.C[:, :c].T + s.C[:, c:c + a] @ g @ s.C[:, c:c + a].T
+        (Jr,), (Kr,) = O.df_jk(s.Bp, s.nao, [D])
+        las = LasDF(dev(s.Bp), s.nao, s.naux, s.nmo, s.ncore, s.nact, precision="split")
+        J, K = las.df_jk_density(dev(Cx), dev(w))
+        las.sync()
+        assert np.abs(J.cpu().numpy() - Jr).max() <= 1e-11 * np.abs(Jr).max()
+        assert np.abs(K.cpu().numpy() - Kr).max() <= 1e-11 * np.abs(Kr).max()
+        las.close()
