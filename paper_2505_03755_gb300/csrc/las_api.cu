@@ -357,18 +357,23 @@ static inline void stage_mark(las_ctx* x, int i) {
 // Chain pieces
 // ------------------------------------------------------------------------------------------
 // S1 + S2 on auxiliary rows [l0, l0+nL): Ht[b][p][mu] = (b^L C_occ)(mu,p), T[b] = C_occ^T H
-static las_status half_and_full(las_ctx* x, int l0, int nL, int want_T, int mark = -1) {
+// H_L = b^L C_occ for the chunk's aux rows, over the first oc columns of C_occ (Ht layout
+// [nL][oc][n]); with want_T (only for oc = op) also T_L = C_occ^T H_L.
+static las_status half_and_full(las_ctx* x, int l0, int nL, int want_T, int mark = -1,
+                                int oc = -1) {
   const int n = x->n, op = x->op;
+  if (oc < 0) oc = op;
+  if (want_T && oc != op) return LAS_ERR_INTERNAL;
   if (x->prec == LAS_SPLIT_BF16) {
-    las_status st = split_half(x->split, l0, nL, x->Ht, x->stream);
+    las_status st = split_half(x->split, l0, nL, oc, x->Ht, x->stream);
     if (st != LAS_OK) return st;
     if (mark >= 0) stage_mark(x, mark);
     return want_T ? split_full(x->split, nL, x->Ht, x->T, x->stream) : LAS_OK;
   }
   PackedSymA A{x->Bp, x->npair, l0};
   StridedA Bm{x->Cocc, 0, op, 1};
-  StridedC Ch{x->Ht, (long)op * n, 1, n, 1.0, 0};
-  gemm_f64(n, op, n, nL, 1, A, Bm, Ch, x->stream);
+  StridedC Ch{x->Ht, (long)oc * n, 1, n, 1.0, 0};
+  gemm_f64(n, oc, n, nL, 1, A, Bm, Ch, x->stream);
   if (mark >= 0) stage_mark(x, mark);
   if (want_T) {
     StridedA Ah{x->Ht, (long)op * n, n, 1};
@@ -485,35 +490,35 @@ extern "C" las_status las_energy_grad_host(las_ctx* x, const double* C_host,
 //         K[mu][nu] = sum_L (b^L D b^L)_{mu nu}   (Eqs. K_1, K_2, with b^L D = H_L C^T).
 static las_status jk_raw(las_ctx* x, int r, double* J, double* K) {
   const int n = x->n, op = x->op;
-  FragInfo fr;
-  memset(&fr, 0, sizeof(fr));
-  fr.ncore = r;
   if (x->prec == LAS_SPLIT_BF16) {
     las_status st = split_prepare_C(x->split, x->Cocc, x->stream);
     if (st != LAS_OK) return st;
   }
+  // the first r columns of C_occ carry the density; `Out` (n x op, idle here) holds them
+  // transposed for the traces of the Coulomb term
+  if (J) launch_transpose_cols(x->Cocc, n, op, r, x->Out, x->stream);
   las_status st;
   for (int l0 = 0; l0 < x->X; l0 += x->Lc) {
     const int nL = std::min(x->Lc, x->X - l0);
-    if ((st = half_and_full(x, l0, nL, J != nullptr)) != LAS_OK) return st;
-    if (J) {  // vc_L = 2 sum_k T_L(k,k) = 2 Tr(b^L D)
-      launch_per_aux(x->T, nL, op, nullptr, nullptr, fr, x->W, x->eps + l0, x->vc + l0,
-                     x->va + l0, 0, nullptr, x->status, x->stream);
-    }
-    if (K && x->prec == LAS_SPLIT_BF16) {  // K = sum_{L,k} H_L(:,k) H_L(:,k)^T
-      if ((st = split_exchange(x->split, nL, x->Ht, K, l0 > 0, x->stream)) != LAS_OK) return st;
+    // H_L over the r density columns only: Ht is [nL][r][n] here
+    if ((st = half_and_full(x, l0, nL, 0, -1, r)) != LAS_OK) return st;
+    // vc_L = 2 sum_k c_k^T H_L(k,:)^T = 2 Tr(b^L D)
+    if (J) launch_trace_ht(x->Ht, x->Out, nL, r, n, x->vc + l0, x->stream);
+    if (K && x->prec == LAS_SPLIT_BF16) {  // K = sum_{L,k} H_L(k,:)^T H_L(k,:)
+      if ((st = split_exchange(x->split, nL, r, x->Ht, K, l0 > 0, x->stream)) != LAS_OK)
+        return st;
     } else if (K) {
       StridedA A{x->Ht, 0, 1, n};
       StridedA B{x->Ht, 0, n, 1};
-      int ks = std::max(1, std::min(x->ksplit, (nL * op) / 64));
+      int ks = std::max(1, std::min(x->ksplit, (nL * r) / 64));
       // reuse `part` as [ks][n][n] only when it is large enough; otherwise accumulate directly
       if ((size_t)ks * n * n <= (size_t)x->ksplit * n * op) {
         StridedC Pk{x->part, (long)n * n, n, 1, 1.0, 0};
-        gemm_f64(n, n, nL * op, 1, ks, A, B, Pk, x->stream);
+        gemm_f64(n, n, nL * r, 1, ks, A, B, Pk, x->stream);
         launch_reduce_partials(x->part, ks, (long)n * n, K, l0 > 0, x->stream);
       } else {
         StridedC Kd{K, 0, n, 1, 1.0, l0 > 0};
-        gemm_f64(n, n, nL * op, 1, 1, A, B, Kd, x->stream);
+        gemm_f64(n, n, nL * r, 1, 1, A, B, Kd, x->stream);
       }
     }
     if ((st = check_launch()) != LAS_OK) return st;
@@ -685,7 +690,9 @@ extern "C" las_status las_autotune(las_ctx* x, const double* C, const double* h,
   if (x->prec != LAS_SPLIT_BF16) return LAS_OK;   // the FP64 path is bound by FP64 arithmetic
   las_status st = las_set_timing(x, 1);
   if (st != LAS_OK) return st;
-  const int cands[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+  // powers-of-two-ish ladder plus the factor that balances the tiles over the SMs
+  const int cands[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64,
+                       split_balanced_ksplit(x->split, x->Lc)};
   int best = split_get_ksplit(x->split);
   float best_ms = 1e30f;
   for (int ks : cands) {

@@ -80,6 +80,11 @@ void launch_pack_cocc(const double* C, int n, int nmo, int o, int op, double* Co
                       cudaStream_t s);
 las_status per_aux_prepare(int nact);
 // gexp == nullptr: W[L][p][q];  otherwise W is written as Wt[q][L*op + p] * 2^gexp[L*op + p]
+// CT[k][mu] = Cocc[mu][k] for k < r (Cocc is n x op)
+void launch_transpose_cols(const double* Cocc, int n, int op, int r, double* CT, cudaStream_t s);
+// vc[b] = 2 sum_{k<r} sum_mu Ht[(b*r + k)*n + mu] * CT[k*n + mu], b < nL (fixed summation order)
+void launch_trace_ht(const double* Ht, const double* CT, int nL, int r, int n, double* vc,
+                     cudaStream_t s);
 void launch_per_aux(const double* T, int nL, int op, const double* dm1s, const double* dm2,
                     const FragInfo& fi, double* W, double* eps, double* vc, double* va,
                     int with_grad, const int* gexp, int* status, cudaStream_t s);

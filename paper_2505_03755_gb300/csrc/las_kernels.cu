@@ -327,6 +327,28 @@ __global__ void k_copy_cols(const double* __restrict__ Ht, int X, int op, int n,
   Lmu[i] = Ht[(L * op + c0 + u) * n + mu];
 }
 
+__global__ void k_transpose_cols(const double* __restrict__ C, int n, int op, int r,
+                                 double* __restrict__ CT) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;   // over r*n, mu fastest
+  if (i >= (long)r * n) return;
+  const int k = (int)(i / n), mu = (int)(i - (long)k * n);
+  CT[i] = C[(long)mu * op + k];
+}
+
+// Coulomb traces: one block per aux row, coalesced along mu, tree reduction in a fixed order.
+__global__ void __launch_bounds__(256)
+k_trace_ht(const double* __restrict__ Ht, const double* __restrict__ CT, int r, int n,
+           double* __restrict__ vc) {
+  __shared__ double red[256];
+  const long b = blockIdx.x;
+  const long cnt = (long)r * n;
+  const double* h = Ht + b * cnt;
+  double acc = 0.0;
+  for (long i = threadIdx.x; i < cnt; i += 256) acc = fma(h[i], CT[i], acc);
+  const double t = block_sum<256>(acc, red);
+  if (threadIdx.x == 0) vc[b] = 2.0 * t;
+}
+
 }  // namespace lasdf
 
 using namespace lasdf;
@@ -376,6 +398,21 @@ void launch_mirror_lower(double* K, int n, cudaStream_t s) {
 void launch_axpy(double* y, const double* x, double a, long count, cudaStream_t s) {
   if (count <= 0) return;
   k_axpy<<<nblk(count, 256), 256, 0, s>>>(y, x, a, count);
+  las_count_launch();
+}
+
+void launch_transpose_cols(const double* Cocc, int n, int op, int r, double* CT,
+                           cudaStream_t s) {
+  const long cnt = (long)r * n;
+  if (cnt <= 0) return;
+  k_transpose_cols<<<nblk(cnt, 256), 256, 0, s>>>(Cocc, n, op, r, CT);
+  las_count_launch();
+}
+
+void launch_trace_ht(const double* Ht, const double* CT, int nL, int r, int n, double* vc,
+                     cudaStream_t s) {
+  if (nL <= 0) return;
+  k_trace_ht<<<nL, 256, 0, s>>>(Ht, CT, r, n, vc);
   las_count_launch();
 }
 

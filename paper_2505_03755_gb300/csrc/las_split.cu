@@ -89,6 +89,7 @@ struct OzParams {
   long ldc, zstride;
   int ht_n, ht_op;
   int lower;               // symmetric product: only tiles that touch the lower triangle
+  long tiles_z;            // tiles per K split (the lower-triangle ones only when lower != 0)
   int sh;                  // fractional bits kept when merging the tail
   int* status;
 };
@@ -118,16 +119,30 @@ __device__ __forceinline__ double make_double(long long W, int E) {
   return __longlong_as_double((long long)bits);
 }
 
+// Column tiles of row tile i that touch the lower triangle (column tile j with j*BN < (i+1)*BM).
+__host__ __device__ __forceinline__ int lower_tiles_in_row(int i, int ntn) {
+  const int c = ((i + 1) * BM + BN - 1) / BN;
+  return c < ntn ? c : ntn;
+}
+
 __device__ __forceinline__ void tile_coords(const OzParams& p, long t, int& m0, int& n0,
                                             int& kb0, int& nkb) {
-  const int ntn = (p.N + BN - 1) / BN, ntm = (p.M + BM - 1) / BM;
-  const long per_z = (long)ntn * ntm;
-  const int z = (int)(t / per_z);
-  const long rem = t - (long)z * per_z;
+  const int ntn = (p.N + BN - 1) / BN;
+  const int z = (int)(t / p.tiles_z);
+  long rem = t - (long)z * p.tiles_z;
   // the column tiles of one row tile are adjacent in tile order so that concurrently running
   // CTAs share that row tile's digit planes through L2
-  m0 = (int)(rem / ntn) * BM;
-  n0 = (int)(rem % ntn) * BN;
+  if (!p.lower) {
+    m0 = (int)(rem / ntn) * BM;
+    n0 = (int)(rem % ntn) * BN;
+  } else {
+    // only the tiles that touch the lower triangle are enumerated, so that the persistent CTAs
+    // share out the work evenly
+    int i = 0;
+    for (int c = lower_tiles_in_row(0, ntn); rem >= c; c = lower_tiles_in_row(++i, ntn)) rem -= c;
+    m0 = i * BM;
+    n0 = (int)rem * BN;
+  }
   kb0 = z * p.kb_per_split;
   nkb = min(p.kb_total, kb0 + p.kb_per_split) - kb0;
 }
@@ -153,7 +168,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long ntiles = (long)((p.N + BN - 1) / BN) * ((p.M + BM - 1) / BM) * p.ksplit;
+  const long ntiles = p.tiles_z * p.ksplit;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
@@ -185,7 +200,6 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int m0, n0, kb0, nkb;
       tile_coords(p, t, m0, n0, kb0, nkb);
-      if (p.lower && n0 >= m0 + BM) continue;
       for (int i = 0; i < nkb; ++i, ++gs) {
         const int st = (int)(gs % NSTAGE);
         if (gs >= NSTAGE && !sm100::mbar_wait(&empty[st], (uint32_t)((gs / NSTAGE) - 1) & 1,
@@ -214,7 +228,6 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int m0, n0, kb0, nkb;
       tile_coords(p, t, m0, n0, kb0, nkb);
-      if (p.lower && n0 >= m0 + BM) continue;
       // the tail accumulator of the previous tile must have been read out
       if (tcount > 0) {
         if (!sm100::mbar_wait(accT, (uint32_t)(tcount - 1) & 1, abort_flag, p.status,
@@ -311,7 +324,6 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int m0, n0, kb0, nkb;
       tile_coords(p, t, m0, n0, kb0, nkb);
-      if (p.lower && n0 >= m0 + BM) continue;
       const int nchunks = (nkb + CHUNK - 1) / CHUNK;
       unsigned long long acc[48];
 #pragma unroll
@@ -604,6 +616,56 @@ k_slice_ht(const double* __restrict__ Ht, long R, int n, Planes Hd, Planes HdT,
   }
 }
 
+// Column maxima of Ht [R][n] over its rows (coalesced along the columns): mx[mu] (atomic max of
+// |x| bit patterns).  Grid: (ceil(n/256), row segments).
+__global__ void __launch_bounds__(256)
+k_colmax(const double* __restrict__ Ht, long R, int n, long seg, unsigned long long* mx) {
+  const int mu = blockIdx.x * 256 + threadIdx.x;
+  if (mu >= n) return;
+  const long r0 = (long)blockIdx.y * seg, r1 = min(R, r0 + seg);
+  unsigned long long m = 0;
+  for (long r = r0; r < r1; ++r) {
+    const unsigned long long b = absbits(Ht[r * n + mu]);
+    m = b > m ? b : m;
+  }
+  if (m) atomicMax(&mx[mu], m);
+}
+
+// Digits of H^T scaled per row mu (exponents from the column maxima): HdT[s](mu, k) for the
+// rows k = (L,p) of Ht, transposed through shared memory.  Block: 32 rows k x all mu.
+__global__ void __launch_bounds__(256)
+k_slice_ht_cols(const double* __restrict__ Ht, long R, int n, const unsigned long long* mx,
+                Planes HdT, int* __restrict__ ex) {
+  __shared__ __nv_bfloat16 tile[NDIG][32][34];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long r0 = (long)blockIdx.x * 32;
+  if (blockIdx.x == 0)
+    for (int mu = threadIdx.x; mu < n; mu += 256) ex[mu] = exp_of_maxbits(mx[mu]);
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int mu = k0 + lane;
+    const int e = mu < n ? exp_of_maxbits(mx[mu]) : 0;
+    for (int i = 0; i < 4; ++i) {
+      const int row = warp + 8 * i;
+      const long r = r0 + row;
+      __nv_bfloat16 d[NDIG];
+      digits_of((r < R && mu < n) ? Ht[r * n + mu] : 0.0, e, d);
+#pragma unroll
+      for (int s = 0; s < NDIG; ++s) tile[s][row][lane] = d[s];
+    }
+    __syncthreads();
+    for (int i = 0; i < 4; ++i) {
+      const int kk = warp * 4 + i;
+      const int m2 = k0 + kk;
+      const long r = r0 + lane;
+      if (m2 < n && r < HdT.nkb * BK) {
+#pragma unroll
+        for (int s = 0; s < NDIG; ++s) HdT.p[HdT.idx(s, m2, r)] = tile[s][lane][kk];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace lasdf_split
 
 using namespace lasdf_split;
@@ -675,6 +737,32 @@ static int num_sms() {
 // out = A * B^T over K: rows [a_row0, a_row0 + M) of A (row exponents ea, or 0 when null),
 // rows [b_row0, b_row0 + N) of B (row exponents eb: the column exponents of the product).
 // mode 0: out[z*zstride + r*ldc + c] (z = K split); mode 1: Ht layout (rows (L, mu)).
+// Output tiles of an M x N product per K split (lower: only those touching the lower triangle).
+static long ozaki_tiles(long M, long N, int lower) {
+  const long ntm = (M + BM - 1) / BM, ntn = (N + BN - 1) / BN;
+  if (!lower) return ntm * ntn;
+  long t = 0;
+  for (long i = 0; i < ntm; ++i) t += lower_tiles_in_row((int)i, (int)ntn);
+  return t;
+}
+
+// K-split factor in [1, cap] that shares `tiles` output tiles of a product with kb K blocks out
+// most evenly over the persistent CTAs: ceil(tiles*ks / SMs) rounds, each of ceil(kb/ks) blocks
+// plus about two chunks of pipeline fill and drain.
+static int balanced_ksplit(long tiles, long kb, long cap) {
+  const long sms = num_sms();
+  int best = 1;
+  double best_t = 1e300;
+  for (long ks = 1; ks <= cap; ++ks) {
+    const double t = (double)((tiles * ks + sms - 1) / sms) * (double)((kb + ks - 1) / ks + 2 * CHUNK);
+    if (t < best_t * (1.0 - 1e-9)) {
+      best_t = t;
+      best = (int)ks;
+    }
+  }
+  return best;
+}
+
 las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const Planes& B,
                       long b_row0, const int* eb, long N, long K, int ksplit, int mode,
                       double* out, long ldc, long zstride, int ht_n, int ht_op, int* status,
@@ -709,12 +797,13 @@ las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const
   p.ht_n = ht_n;
   p.ht_op = ht_op;
   p.lower = lower;
+  p.tiles_z = ozaki_tiles(M, N, lower);
   // fractional bits kept for the tail: |fixed-point sum| < 2^38 * (k per CTA) must fit 62 bits
   int lgk = 0;
   while ((1L << lgk) < (long)p.kb_per_split * BK) ++lgk;
   p.sh = std::max(0, std::min(20, 61 - 14 - 8 * (NEXACT - 1) - lgk));
   p.status = status;
-  const long tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM) * (long)ksplit;
+  const long tiles = p.tiles_z * ksplit;
   dim3 grid((unsigned)std::min<long>(tiles, num_sms()), 1, 1);   // persistent: one CTA per SM
   k_ozaki<<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, p);
   las_count_launch();
@@ -802,16 +891,15 @@ las_status split_create(SplitState** out, int n, int X, int op, int Lc, const do
   s->op = op;
   s->Lc = Lc;
   s->status = status;
-  {
-    const long tiles = ((n + BM - 1) / BM) * ((op + BN - 1) / BN);
-    s->ks = (int)std::max(1L, std::min(64L, (2 * 148 + tiles - 1) / tiles));
-    s->ksplit6 = 64;
-  }
+  s->ksplit6 = 64;
   // one-time launch attributes, so that later calls can be captured into CUDA graphs
   if (ozaki_prepare() != LAS_OK || num_sms() <= 0) {
     free(s);
     return LAS_ERR_CUDA;
   }
+  // projection split-K (autotunable): output n x op, K = the (L, p) rows of one chunk
+  s->ks = balanced_ksplit(ozaki_tiles(n, op, 0), ((long)Lc * op + BK - 1) / BK,
+                          std::min<long>(s->ksplit6, std::max(1L, ((long)Lc * op) / 2048)));
   size_t total = 0;
   las_status rc = LAS_OK;
   auto A = [&](void** p, size_t b) {
@@ -873,6 +961,10 @@ void split_destroy(SplitState* s) {
 const int* split_hexp(SplitState* s) { return s->Hexp; }
 
 int split_get_ksplit(SplitState* s) { return s->ks; }
+int split_balanced_ksplit(SplitState* s, int nL) {
+  return balanced_ksplit(ozaki_tiles(s->n, s->op, 0), ((long)nL * s->op + BK - 1) / BK,
+                         std::min<long>(s->ksplit6, std::max(1L, ((long)nL * s->op) / 2048)));
+}
 void split_set_ksplit(SplitState* s, int ks) { s->ks = std::max(1, std::min(ks, s->ksplit6)); }
 
 las_status split_prepare_C(SplitState* s, const double* Cocc, cudaStream_t st) {
@@ -881,10 +973,11 @@ las_status split_prepare_C(SplitState* s, const double* Cocc, cudaStream_t st) {
   return slice_rows(acc, s->Cdig, s->Cexp, st);
 }
 
-las_status split_half(SplitState* s, int l0, int nL, double* Ht, cudaStream_t st) {
+las_status split_half(SplitState* s, int l0, int nL, int oc, double* Ht, cudaStream_t st) {
   const long rows = (long)nL * s->n;
+  if (oc < 1 || oc > s->op) return LAS_ERR_INTERNAL;
   return ozaki_gemm(s->Bdig, (long)l0 * s->n, s->Bexp + (long)l0 * s->n, rows, s->Cdig, 0,
-                    s->Cexp, s->op, s->n, 1, 1, Ht, 0, 0, s->n, s->op, s->status, st);
+                    s->Cexp, oc, s->n, 1, 1, Ht, 0, 0, s->n, oc, s->status, st);
 }
 
 las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaStream_t st) {
@@ -923,20 +1016,36 @@ las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, i
   return LAS_OK;
 }
 
-las_status split_exchange(SplitState* s, int nL, const double* Ht, double* K, int accumulate,
+las_status split_exchange(SplitState* s, int nL, int oc, const double* Ht, double* K, int accumulate,
                           cudaStream_t st) {
   // K(mu,nu) (+)= sum_{(L,p)} Ht[(L,p)][mu] Ht[(L,p)][nu]: rows mu of H^T, scaled per row over
   // the long index (L,p), serve as both operands
-  const long R = (long)nL * s->op, n = s->n;
+  const long R = (long)nL * oc, n = s->n;
+  if (oc < 1 || oc > s->op) return LAS_ERR_INTERNAL;
   Planes HT = s->HdigT;
   HT.K = R;
-  las_status rc = slice_rows(RowsStrided{Ht, 1, n, nullptr}, HT, s->hexp, st, s->mx);
-  if (rc != LAS_OK) return rc;
+  las_status rc = LAS_OK;
+  {
+    cudaError_t e = cudaMemsetAsync(s->mx, 0, n * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) {
+      las_record_cuda_error(e, "cudaMemsetAsync(colmax)", __FILE__, __LINE__);
+      return LAS_ERR_CUDA;
+    }
+    const long seg = 512;
+    dim3 g1((unsigned)((n + 255) / 256), (unsigned)((R + seg - 1) / seg));
+    k_colmax<<<g1, 256, 0, st>>>(Ht, R, (int)n, seg, s->mx);
+    las_count_launch();
+    k_slice_ht_cols<<<(unsigned)((R + 31) / 32), 256, 0, st>>>(Ht, R, (int)n, s->mx, HT, s->hexp);
+    las_count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      las_record_cuda_error(e, "k_slice_ht_cols launch", __FILE__, __LINE__);
+      return LAS_ERR_CUDA;
+    }
+  }
   // partials [ks][n][n] live in the projection's partial buffer (64 * n * op doubles)
-  const long cap = std::max(1L, (64L * s->op) / n);
-  const long tiles = ((n + BM - 1) / BM) * ((n + BN - 1) / BN);
-  const int ks = (int)std::max(1L, std::min(cap, std::min((2L * num_sms() + tiles - 1) / tiles,
-                                                          (R + 32 * 64 - 1) / (32 * 64))));
+  const long cap = std::max(1L, std::min((64L * s->op) / n, (R + 32 * 64 - 1) / (32 * 64)));
+  const int ks = balanced_ksplit(ozaki_tiles(n, n, 1), (R + BK - 1) / BK, cap);
   // symmetric product: only tiles touching the lower triangle; the caller mirrors the result
   rc = ozaki_gemm(HT, 0, s->hexp, n, HT, 0, s->hexp, n, R, ks, 0, s->part, n, n * n, 0, 0,
                   s->status, st, 1);

@@ -16,15 +16,18 @@ const int* split_hexp(SplitState* s);
 void split_destroy(SplitState* s);
 las_status split_prepare_C(SplitState* s, const double* Cocc, cudaStream_t st);
 // S1: Ht[b][p][mu] = sum_nu b^{l0+b}(mu,nu) C_occ(nu,p)   (b < nL)
-las_status split_half(SplitState* s, int l0, int nL, double* Ht, cudaStream_t st);
+// H for aux rows l0..l0+nL of the first oc columns of C_occ, Ht layout [nL][oc][n]
+las_status split_half(SplitState* s, int l0, int nL, int oc, double* Ht, cudaStream_t st);
 // S2: T[b] = Ht[b] C_occ   (op x op per b)
 las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaStream_t st);
 // K (+)= sum_{(L,p)} H(mu,(L,p)) H(nu,(L,p)) over the chunk's half transform Ht[(L,p)][mu];
 // only the lower triangle (mu >= nu) is valid: mirror it afterwards
-las_status split_exchange(SplitState* s, int nL, const double* Ht, double* K, int accumulate,
+las_status split_exchange(SplitState* s, int nL, int oc, const double* Ht, double* K, int accumulate,
                           cudaStream_t st);
 // split-K factor of the projection GEMM (1..64)
 int split_get_ksplit(SplitState* s);
+// split-K of the projection that shares its tiles out most evenly over the SMs for nL aux rows
+int split_balanced_ksplit(SplitState* s, int nL);
 void split_set_ksplit(SplitState* s, int ks);
 // hC = h C_occ and hmo = C_occ^T hC (split_prepare_C must have run for this C)
 las_status split_one_electron(SplitState* s, const double* h, double* hC, double* hmo,
