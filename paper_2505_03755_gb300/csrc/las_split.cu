@@ -94,29 +94,14 @@ struct OzParams {
   int* status;
 };
 
+// W * 2^E rounded once to FP64 (round to nearest even): the hardware int64 -> FP64 conversion,
+// then an exponent-field shift (exact for normal results; the rare others go through ldexp).
 __device__ __forceinline__ double make_double(long long W, int E) {
-  if (W == 0) return 0.0;
-  unsigned long long sgn = W < 0 ? (1ull << 63) : 0ull;
-  unsigned long long m = W < 0 ? (unsigned long long)(-W) : (unsigned long long)W;
-  int lz = __clzll((long long)m);
-  m <<= lz;
-  int e = 63 - lz + E;
-  unsigned long long mant = m >> 11;
-  unsigned long long rem = m & 0x7FFull;
-  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) {
-    mant += 1;
-    if (mant >> 53) {
-      mant >>= 1;
-      e += 1;
-    }
-  }
-  int eb = e + 1023;
-  if (eb <= 0 || eb >= 2047) {  // outside the normal range: slow but exact path
-    const double v = ldexp((double)mant, e - 52);
-    return sgn ? -v : v;
-  }
-  unsigned long long bits = sgn | ((unsigned long long)eb << 52) | (mant & ((1ull << 52) - 1));
-  return __longlong_as_double((long long)bits);
+  const double v = __ll2double_rn(W);
+  const long long b = __double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0 || ex + E <= 0 || ex + E >= 2047) return ldexp(v, E);
+  return __longlong_as_double(b + ((long long)E << 52));
 }
 
 // Column tiles of row tile i that touch the lower triangle (column tile j with j*BN < (i+1)*BM).
@@ -262,7 +247,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
         const bool last_in_chunk = (i % CHUNK) == CHUNK - 1 || i == nkb - 1;
         if (need_acce) {
           if (!last_in_chunk && npend < NSTAGE - 1 &&
-              !sm100::mbar_try_wait(acce, (uint32_t)(gc - 1) & 1)) {
+              !sm100::mbar_test_wait(acce, (uint32_t)(gc - 1) & 1)) {
             if (npend == 0) {
               pend0 = gs;
               pend_i0 = i;
@@ -355,20 +340,23 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
           if (lane == 0) sm100::mbar_arrive(accT);
           extra = p.sh;
         }
+        // exact groups: integers g_q (|g_q| <= 2^24) in units of 2^-8q, merged as
+        // V = ((g_0 2^8 + g_1) 2^8 + g_2) 2^8 + g_3 (the first step fits 32 bits)
+        static_assert(NEXACT == 4, "the merge below is written for four exact groups");
 #pragma unroll
-        for (int q = 0; q < NEXACT; ++q) {
-          const float up = __int_as_float((127 + 8 * q) << 23);   // 2^(8q)
-          const int shq = 8 * (NEXACT - 1 - q) + extra;
+        for (int j = 0; j < 3; ++j) {
+          uint32_t r[NEXACT][16];
 #pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            uint32_t r[16];
-            sm100::tmem_ld16(tl + COL_EXACT0 + q * BN + j * 16, r);
-            sm100::tmem_wait_ld();
+          for (int q = 0; q < NEXACT; ++q) sm100::tmem_ld16(tl + COL_EXACT0 + q * BN + j * 16, r[q]);
+          sm100::tmem_wait_ld();
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const int iv = __float2int_rn(__uint_as_float(r[e]) * up);
-              acc[j * 16 + e] += (unsigned long long)(long long)iv << shq;
-            }
+          for (int e = 0; e < 16; ++e) {
+            const int g0 = __float2int_rn(__uint_as_float(r[0][e]));
+            const int g1 = __float2int_rn(__uint_as_float(r[1][e]) * 256.0f);
+            const int g2 = __float2int_rn(__uint_as_float(r[2][e]) * 65536.0f);
+            const int g3 = __float2int_rn(__uint_as_float(r[3][e]) * 16777216.0f);
+            const long long v = (long long)(g0 * 256 + g1) * 65536 + (long long)g2 * 256 + g3;
+            acc[j * 16 + e] += (unsigned long long)v << extra;
           }
         }
         sm100::tc_fence_before();
