@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256)
 k_per_aux(const double* __restrict__ T, int nL, int op, const double* __restrict__ dm1s,
           const double* __restrict__ dm2, FragInfo fi, double* __restrict__ W,
           double* __restrict__ eps, double* __restrict__ vcv, double* __restrict__ vav,
-          int with_grad, const int* __restrict__ gexp, int* status) {
+          int with_grad, const int* __restrict__ gexp, int* status, int use_p) {
   extern __shared__ double sm[];
   const int a = fi.nact, c = fi.ncore, o = c + a;
   double* Taa = sm;             // a*a
@@ -63,6 +63,7 @@ k_per_aux(const double* __restrict__ T, int nL, int op, const double* __restrict
   double* Y = Ds + a * a;       // a*a
   double* red = Y + a * a;      // 256
   double* cK = red + 256;       // nfrag
+  double* P = cK + LAS_MAX_FRAG;  // a*a when the launch provides it (fast cross-fragment path)
   const long Lb = blockIdx.x;
   const double* TL = T + Lb * (long)op * op;
   const int tid = threadIdx.x;
@@ -108,7 +109,9 @@ k_per_aux(const double* __restrict__ T, int nL, int op, const double* __restrict
     const int K = frag_of(fi, u), Kp = frag_of(fi, v);
     const int oK = fi.off[K], mK = fi.off[K + 1] - oK;
     double y = 0.0;
-    if (K == Kp) {
+    if (K != Kp && use_p) {
+      // cross-fragment blocks come from the factored form below
+    } else if (K == Kp) {
       const double* g2 = dm2 + fi.dm2_off[K];
       const int uu = u - oK, vv = v - oK;
       const double* gr = g2 + ((long)uu * mK + vv) * mK * mK;
@@ -134,6 +137,34 @@ k_per_aux(const double* __restrict__ T, int nL, int op, const double* __restrict
       }
     }
     Y[i] = y;
+  }
+  if (use_p) {
+    // -sum_sigma gK_s (T_KK' gK'_s) for K != K': P_s = T_aa blockdiag(g_s) first (a*a*m work),
+    // then the left factor, instead of the inner sum per (u, v)
+    for (int sg = 0; sg < 2; ++sg) {
+      __syncthreads();
+      for (int i = tid; i < a * a; i += 256) {
+        const int x = i / a, v = i % a;
+        const int Kp = frag_of(fi, v), oP = fi.off[Kp], mP = fi.off[Kp + 1] - oP;
+        const double* gPs = dm1s + fi.dm1_off[Kp] + sg * mP * mP;
+        const int vv = v - oP;
+        double t = 0.0;
+        for (int w = 0; w < mP; ++w) t += Taa[x * a + oP + w] * gPs[w * mP + vv];
+        P[i] = t;
+      }
+      __syncthreads();
+      for (int i = tid; i < a * a; i += 256) {
+        const int u = i / a, v = i % a;
+        const int K = frag_of(fi, u), Kp = frag_of(fi, v);
+        if (K == Kp) continue;
+        const int oK = fi.off[K], mK = fi.off[K + 1] - oK;
+        const double* gKs = dm1s + fi.dm1_off[K] + sg * mK * mK;
+        const int uu = u - oK;
+        double t = 0.0;
+        for (int x = 0; x < mK; ++x) t += gKs[uu * mK + x] * P[(oK + x) * a + v];
+        Y[i] -= t;
+      }
+    }
   }
   __syncthreads();
 
@@ -361,10 +392,16 @@ void launch_pack_cocc(const double* C, int n, int nmo, int o, int op, double* Co
   las_count_launch();
 }
 
+#define LAS_PER_AUX_FAST_MAX_ACT 84
+static size_t per_aux_fast_smem(int a) {
+  return (4 * (size_t)a * a + 256 + LAS_MAX_FRAG) * sizeof(double);
+}
+
 las_status per_aux_prepare(int nact) {
   // always the largest supported size, so that contexts with different active spaces coexist
   (void)nact;
   size_t smem = (3 * (size_t)LAS_MAX_ACT * LAS_MAX_ACT + 256 + LAS_MAX_FRAG) * sizeof(double);
+  smem = std::max(smem, per_aux_fast_smem(LAS_PER_AUX_FAST_MAX_ACT));
   cudaError_t e = cudaFuncSetAttribute(k_per_aux, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)std::max<size_t>(smem, 48 * 1024));
   if (e != cudaSuccess) {
@@ -378,9 +415,12 @@ void launch_per_aux(const double* T, int nL, int op, const double* dm1s, const d
                     const FragInfo& fi, double* W, double* eps, double* vc, double* va,
                     int with_grad, const int* gexp, int* status, cudaStream_t s) {
   if (nL <= 0) return;
-  size_t smem = (3 * (size_t)fi.nact * fi.nact + 256 + LAS_MAX_FRAG) * sizeof(double);
+  // the factored cross-fragment path needs one more a*a buffer; it fits for a <= 84
+  const int use_p = fi.nfrag > 1 && fi.nact <= LAS_PER_AUX_FAST_MAX_ACT;
+  size_t smem = use_p ? per_aux_fast_smem(fi.nact)
+                      : (3 * (size_t)fi.nact * fi.nact + 256 + LAS_MAX_FRAG) * sizeof(double);
   k_per_aux<<<nL, 256, smem, s>>>(T, nL, op, dm1s, dm2, fi, W, eps, vc, va, with_grad, gexp,
-                                  status);
+                                  status, use_p);
   las_count_launch();
 }
 

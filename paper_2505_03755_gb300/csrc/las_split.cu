@@ -460,9 +460,15 @@ __device__ __forceinline__ void digits_of(double xv, int e, __nv_bfloat16 (&out)
     hi = (hi - t) >> 8;
   }
   d[0] = hi;
+  // d_s * 2^-8s as BF16 without conversion instructions: the float of d_s from the bit pattern
+  // of 1.5*2^23 + d_s (exact for |d_s| < 2^22), scaled by a power of two, and its upper half
+  // (exact: at most 8 significant bits)
 #pragma unroll
-  for (int s = 0; s < NDIG; ++s)
-    out[s] = __float2bfloat16_rn((float)d[s] * __int_as_float((127 - 8 * s) << 23));
+  for (int s = 0; s < NDIG; ++s) {
+    const float f = (__int_as_float(0x4B400000 + d[s]) - 12582912.0f) *
+                    __int_as_float((127 - 8 * s) << 23);
+    out[s] = __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
+  }
 }
 
 __device__ __forceinline__ int exp_of_maxbits(unsigned long long mx) {
@@ -473,14 +479,14 @@ __device__ __forceinline__ unsigned long long absbits(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
 
-// Short rows: one warp per row r < Rpad (rows >= R are written as zeros); exponent e_r with
-// max|x| < 2^e_r for r < R, digit planes for every k < nkb*BK (zero beyond K).
+// Short rows: one warp per row r < rows (rows >= R are written as zeros); exponent e_r with
+// max|x| < 2^e_r for r < R, digit planes for every k < kb*BK (zero beyond K).
 template <class Acc>
 __global__ void __launch_bounds__(256)
-k_slice_rows(Acc acc, Planes P, int* ex) {
+k_slice_rows(Acc acc, Planes P, long rows, long kb, int* ex) {
   const long r = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (r >= P.Rpad) return;
+  if (r >= rows) return;
   const bool live = r < P.R;
   unsigned long long mx = 0;
   if (live)
@@ -495,7 +501,7 @@ k_slice_rows(Acc acc, Planes P, int* ex) {
   }
   const int e = exp_of_maxbits(mx);
   if (lane == 0 && live) ex[r] = e;
-  const long kend = P.nkb * BK;
+  const long kend = kb * BK;
   for (long k = lane; k < kend; k += 32) {
     __nv_bfloat16 d[NDIG];
     digits_of((live && k < P.K) ? acc(r, k) : 0.0, e, d);
@@ -529,15 +535,15 @@ k_rowmax_long(Acc acc, long K, long seg, unsigned long long* mx) {
   }
 }
 
-// Long rows, pass 2: element-parallel digits over Rpad x nkb*BK (zeros outside R x K).
+// Long rows, pass 2: element-parallel digits over rows x kb*BK (zeros outside R x K).
 template <class Acc>
 __global__ void __launch_bounds__(256)
-k_digits_long(Acc acc, Planes P, const unsigned long long* mx, int* ex) {
-  const long kend = P.nkb * BK;
+k_digits_long(Acc acc, Planes P, long rows, long kbc, const unsigned long long* mx, int* ex) {
+  const long kend = kbc * BK;
   const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (i >= P.Rpad * kend) return;
+  if (i >= rows * kend) return;
   // thread order follows the K-blocked output: (k block, row, k within the block)
-  const long kb = i / (P.Rpad * BK), rem = i - kb * (P.Rpad * BK);
+  const long kb = i / (rows * BK), rem = i - kb * (rows * BK);
   const long r = rem / BK, k = kb * BK + (rem - r * BK);
   const bool live = r < P.R;
   const int e = live ? exp_of_maxbits(mx[r]) : 0;
@@ -549,12 +555,14 @@ k_digits_long(Acc acc, Planes P, const unsigned long long* mx, int* ex) {
 }
 
 // Half-transformed rows (L,p) of Ht [R][n]: exponents, digit planes Hd (rows (L,p), K = mu) and
-// the same digits transposed, HdT (rows mu, K = (L,p)), in one pass.  Block: 32 rows, 8 warps.
-// Rows mu >= n of HdT are never written (they stay zero from set-up).
+// the same digits transposed, HdT (rows mu, K = (L,p)), in one pass.  Block: 32 rows r, 256
+// threads; per 64-column step each warp cuts 8 columns of all 32 rows (16-byte stores into Hd),
+// then 16-byte stores of 8 consecutive rows r into HdT from a transposed shared tile.  Rows of Hd
+// beyond the block's 32 and rows mu >= n of HdT are never written (they stay zero from set-up).
 __global__ void __launch_bounds__(256)
 k_slice_ht(const double* __restrict__ Ht, long R, int n, Planes Hd, Planes HdT,
            int* __restrict__ ex) {
-  __shared__ __nv_bfloat16 tile[NDIG][32][34];
+  __shared__ __align__(16) __nv_bfloat16 tile[NDIG][64][40];   // [s][column k][row r] (+8 pad)
   __shared__ int es[32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long r0 = (long)blockIdx.x * 32;
@@ -578,27 +586,36 @@ k_slice_ht(const double* __restrict__ Ht, long R, int n, Planes Hd, Planes HdT,
     }
   }
   __syncthreads();
-  const long kend = Hd.nkb * BK;
-  for (long k0 = 0; k0 < kend; k0 += 32) {
-    for (int i = 0; i < 4; ++i) {
-      const int row = warp + 8 * i;
-      const long r = r0 + row, k = k0 + lane;
-      __nv_bfloat16 d[NDIG];
-      digits_of((r < R && k < n) ? Ht[r * n + k] : 0.0, es[row], d);
+  const long kend = Hd.nkb * BK;            // a multiple of 16
+  const long r = r0 + lane;                 // phase A: this thread's row
+  const bool live = r < R;
+  const int e = es[lane];
+  const double* hrow = Ht + r * n;
+  const int kk = threadIdx.x >> 2, r8 = (threadIdx.x & 3) * 8;   // phase B: column, 8 rows
+  for (long k0 = 0; k0 < kend; k0 += 64) {
+    const long k = k0 + warp * 8;
+    if (k < kend) {
+      __nv_bfloat16 d[8][NDIG];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) digits_of((live && k + j < n) ? hrow[k + j] : 0.0, e, d[j]);
 #pragma unroll
       for (int s = 0; s < NDIG; ++s) {
-        tile[s][row][lane] = d[s];
-        if (r < Hd.Rpad && k < kend) Hd.p[Hd.idx(s, r, k)] = d[s];
+        uint4 v;
+        __nv_bfloat16* pv = (__nv_bfloat16*)&v;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          pv[j] = d[j][s];
+          tile[s][warp * 8 + j][lane] = d[j][s];
+        }
+        if (r < Hd.Rpad) *(uint4*)(Hd.p + Hd.idx(s, r, k)) = v;
       }
     }
     __syncthreads();
-    for (int i = 0; i < 4; ++i) {
-      const int kk = warp * 4 + i;
-      const long k = k0 + kk, r = r0 + lane;
-      if (k < n && r < HdT.nkb * BK) {
+    const long mu = k0 + kk;
+    if (mu < n && r0 + r8 < HdT.nkb * BK) {
 #pragma unroll
-        for (int s = 0; s < NDIG; ++s) HdT.p[HdT.idx(s, k, r)] = tile[s][lane][kk];
-      }
+      for (int s = 0; s < NDIG; ++s)
+        *(uint4*)(HdT.p + HdT.idx(s, mu, r0 + r8)) = *(const uint4*)&tile[s][kk][r8];
     }
     __syncthreads();
   }
@@ -803,10 +820,14 @@ las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const
   return LAS_OK;
 }
 
+// live_only: only rows < R and the K blocks that hold K are written (planes whose padding rows
+// were zeroed at set-up); otherwise every padded row and K block of the layout is written.
 template <class Acc>
 static las_status slice_rows(Acc acc, const Planes& P, int* ex, cudaStream_t st,
-                             unsigned long long* mx_ws = nullptr) {
+                             unsigned long long* mx_ws = nullptr, bool live_only = false) {
   if (P.R <= 0) return LAS_OK;
+  const long rows = live_only ? P.R : P.Rpad;
+  const long kbc = live_only ? std::min(P.nkb, planes_nkb(P.K)) : P.nkb;
   if (P.K > 8192 && mx_ws && P.R <= 65535) {
     // long rows: block-parallel maxima, then element-parallel digits
     cudaError_t e0 = cudaMemsetAsync(mx_ws, 0, P.R * sizeof(unsigned long long), st);
@@ -818,12 +839,13 @@ static las_status slice_rows(Acc acc, const Planes& P, int* ex, cudaStream_t st,
     dim3 g1((unsigned)((P.K + seg - 1) / seg), (unsigned)P.R);
     k_rowmax_long<Acc><<<g1, 256, 0, st>>>(acc, P.K, seg, mx_ws);
     las_count_launch();
-    const long tot = P.Rpad * P.nkb * BK;
-    k_digits_long<Acc><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(acc, P, mx_ws, ex);
+    const long tot = rows * kbc * BK;
+    k_digits_long<Acc><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(acc, P, rows, kbc, mx_ws,
+                                                                       ex);
     las_count_launch();
   } else {
-    const long threads = P.Rpad * 32;
-    k_slice_rows<Acc><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(acc, P, ex);
+    const long threads = rows * 32;
+    k_slice_rows<Acc><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(acc, P, rows, kbc, ex);
     las_count_launch();
   }
   cudaError_t e = cudaGetLastError();
@@ -917,11 +939,17 @@ las_status split_create(SplitState** out, int n, int X, int op, int Lc, const do
   A((void**)&s->hexp, (size_t)n * 4);
   A(&q, planes_bytes(op, n));        s->hcdig = make_planes(q, op, n);  q = nullptr;
   A((void**)&s->hcexp, (size_t)op * 4);
-  if (rc == LAS_OK) {
-    // rows mu >= n of the transposed planes are never written: make them zero once
-    cudaError_t e = cudaMemsetAsync(s->HdigT.p, 0, planes_bytes(n, R), st);
+  // rows mu >= n of the transposed planes and the padding rows of C, W, h and (h C)^T are never
+  // written by the per-evaluation slicers: make them zero once
+  const struct { void* p; size_t b; } zero[] = {
+      {s->HdigT.p, planes_bytes(n, R)}, {s->Wdig.p, planes_bytes(op, R)},
+      {s->Cdig.p, planes_bytes(op, n)}, {s->hdig.p, planes_bytes(n, n)},
+      {s->hcdig.p, planes_bytes(op, n)}};
+  for (const auto& z : zero) {
+    if (rc != LAS_OK) break;
+    cudaError_t e = cudaMemsetAsync(z.p, 0, z.b, st);
     if (e != cudaSuccess) {
-      las_record_cuda_error(e, "cudaMemsetAsync(HdigT)", __FILE__, __LINE__);
+      las_record_cuda_error(e, "cudaMemsetAsync(split planes)", __FILE__, __LINE__);
       rc = LAS_ERR_CUDA;
     }
   }
@@ -958,7 +986,7 @@ void split_set_ksplit(SplitState* s, int ks) { s->ks = std::max(1, std::min(ks, 
 las_status split_prepare_C(SplitState* s, const double* Cocc, cudaStream_t st) {
   // rows p of C_occ^T (K = nu): element (p, nu) = Cocc[nu*op + p]
   RowsStrided acc{Cocc, 1, s->op, nullptr};
-  return slice_rows(acc, s->Cdig, s->Cexp, st);
+  return slice_rows(acc, s->Cdig, s->Cexp, st, nullptr, true);
 }
 
 las_status split_half(SplitState* s, int l0, int nL, int oc, double* Ht, cudaStream_t st) {
@@ -994,7 +1022,7 @@ las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, i
   Planes W = s->Wdig;
   W.K = R;
   RowsStrided acc{Wt, R, 1, nullptr};
-  las_status rc = slice_rows(acc, W, s->Wexp, st, s->mx);
+  las_status rc = slice_rows(acc, W, s->Wexp, st, s->mx, true);
   if (rc != LAS_OK) return rc;
   const int ks = (int)std::max(1L, std::min((long)s->ks, (R + 32 * 64 - 1) / (32 * 64)));
   rc = ozaki_gemm(s->HdigT, 0, nullptr, s->n, W, 0, s->Wexp, s->op, R, ks, 0, s->part, s->op,
@@ -1045,13 +1073,14 @@ las_status split_exchange(SplitState* s, int nL, int oc, const double* Ht, doubl
 las_status split_one_electron(SplitState* s, const double* h, double* hC, double* hmo,
                               cudaStream_t st) {
   // hC = h C_occ  (rows mu of h, columns p of C_occ: the digits of C_occ are already sliced)
-  las_status rc = slice_rows(RowsStrided{h, s->n, 1, nullptr}, s->hdig, s->hexp, st);
+  las_status rc = slice_rows(RowsStrided{h, s->n, 1, nullptr}, s->hdig, s->hexp, st, nullptr,
+                             true);
   if (rc == LAS_OK)
     rc = ozaki_gemm(s->hdig, 0, s->hexp, s->n, s->Cdig, 0, s->Cexp, s->op, s->n, 1, 0, hC, s->op,
                     0, 0, 0, s->status, st);
   // hmo = C_occ^T hC  (rows p of C_occ^T are the C_occ digit rows; columns q of hC)
   if (rc == LAS_OK)
-    rc = slice_rows(RowsStrided{hC, 1, s->op, nullptr}, s->hcdig, s->hcexp, st);
+    rc = slice_rows(RowsStrided{hC, 1, s->op, nullptr}, s->hcdig, s->hcexp, st, nullptr, true);
   if (rc == LAS_OK)
     rc = ozaki_gemm(s->Cdig, 0, s->Cexp, s->op, s->hcdig, 0, s->hcexp, s->op, s->n, 1, 0, hmo,
                     s->op, 0, 0, 0, s->status, st);
