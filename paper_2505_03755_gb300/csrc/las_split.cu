@@ -43,7 +43,11 @@ constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256;
 constexpr int TMEM_COLS = 512;
 constexpr int COL_EXACT0 = 0;    // exact groups q = 0..3 at 0, 96, 192, 288; tail at 384
 constexpr int COL_TAIL = NEXACT * BN;
-constexpr int NTHREADS = 320;    // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int EPI_WARPS = 16;    // epilogue warps: 4 column groups x 4 TMEM lane quarters
+constexpr int EPI_COLS = BN * 4 / EPI_WARPS;   // 24 accumulator columns per epilogue thread
+constexpr int EPI_STEP = 8;      // columns per TMEM load
+static_assert(EPI_COLS == 3 * EPI_STEP, "three loads per accumulator slice");
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;   // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
 constexpr uint32_t IDESC = sm100::idesc_bf16(BM, BN);
 
 // Digit planes are stored K-blocked: element (s, r, k) of an operand with R rows lives at
@@ -133,7 +137,7 @@ __device__ __forceinline__ void tile_coords(const OzParams& p, long t, int& m0, 
 }
 
 // Persistent CTAs (one per SM) walk the tiles (row tile, column tile, K split).  Roles:
-// warp 0 streams digit-plane stages with TMA, warp 1 issues tcgen05.mma, warps 2..9 drain the
+// warp 0 streams digit-plane stages with TMA, warp 1 issues tcgen05.mma, warps 2..17 drain the
 // TMEM accumulators.  Stage, chunk and tile counters run on across tiles so that the loads of the
 // next tile overlap the last MMAs of the current one, and its MMAs overlap the current tile's
 // conversion and stores.
@@ -161,8 +165,8 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
       sm100::mbar_init(&empty[s], 1);
     }
     sm100::mbar_init(accf, 1);
-    sm100::mbar_init(acce, 8);
-    sm100::mbar_init(accT, 8);
+    sm100::mbar_init(acce, EPI_WARPS);
+    sm100::mbar_init(accT, EPI_WARPS);
     sm100::mbar_init(drain, 1);
     *abort_flag = 0;
     sm100::fence_mbar_init();
@@ -299,10 +303,10 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     sm100::mma_commit(drain);
     sm100::mbar_wait(drain, 0, abort_flag, p.status, LAS_ERR_TIMEOUT);
   } else if (warp >= 2) {
-    // ---------------- epilogue (8 warps) ----------------
+    // ---------------- epilogue (16 warps) ----------------
     const int lq = warp & 3;                 // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;        // columns [half*48, half*48+48)
-    const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + half * 48;
+    const int cg = (warp - 2) >> 2;          // columns [cg*EPI_COLS, (cg+1)*EPI_COLS)
+    const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + cg * EPI_COLS;
     const float tscale = __int_as_float((127 + 8 * (NEXACT - 1) + p.sh) << 23);  // 2^(24+sh)
     long gc = 0;
     bool ok = true;
@@ -310,9 +314,9 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
       int m0, n0, kb0, nkb;
       tile_coords(p, t, m0, n0, kb0, nkb);
       const int nchunks = (nkb + CHUNK - 1) / CHUNK;
-      unsigned long long acc[48];
+      unsigned long long acc[EPI_COLS];
 #pragma unroll
-      for (int j = 0; j < 48; ++j) acc[j] = 0;
+      for (int j = 0; j < EPI_COLS; ++j) acc[j] = 0;
       for (int c = 0; c < nchunks; ++c, ++gc) {
         if (!sm100::mbar_wait(accf, (uint32_t)gc & 1, abort_flag, p.status, LAS_ERR_TIMEOUT,
                               256)) {
@@ -325,16 +329,17 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
         if (fin) {
           // tail first, so that the next tile's tail MMAs can start:
           // acc <- acc * 2^sh + rint(tail * 2^(24+sh))  (int64, modulo 2^64)
+          uint32_t r[3][EPI_STEP];
 #pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            uint32_t r[16];
-            sm100::tmem_ld16(tl + COL_TAIL + j * 16, r);
-            sm100::tmem_wait_ld();
+          for (int j = 0; j < 3; ++j) sm100::tmem_ld8(tl + COL_TAIL + j * EPI_STEP, r[j]);
+          sm100::tmem_wait_ld();
 #pragma unroll
-            for (int e = 0; e < 16; ++e)
-              acc[j * 16 + e] = (acc[j * 16 + e] << p.sh) +
-                                (unsigned long long)__float2ll_rn(__uint_as_float(r[e]) * tscale);
-          }
+          for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int e = 0; e < EPI_STEP; ++e)
+              acc[j * EPI_STEP + e] =
+                  (acc[j * EPI_STEP + e] << p.sh) +
+                  (unsigned long long)__float2ll_rn(__uint_as_float(r[j][e]) * tscale);
           sm100::tc_fence_before();
           __syncwarp();
           if (lane == 0) sm100::mbar_arrive(accT);
@@ -345,18 +350,19 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
         static_assert(NEXACT == 4, "the merge below is written for four exact groups");
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-          uint32_t r[NEXACT][16];
+          uint32_t r[NEXACT][EPI_STEP];
 #pragma unroll
-          for (int q = 0; q < NEXACT; ++q) sm100::tmem_ld16(tl + COL_EXACT0 + q * BN + j * 16, r[q]);
+          for (int q = 0; q < NEXACT; ++q)
+            sm100::tmem_ld8(tl + COL_EXACT0 + q * BN + j * EPI_STEP, r[q]);
           sm100::tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
+          for (int e = 0; e < EPI_STEP; ++e) {
             const int g0 = __float2int_rn(__uint_as_float(r[0][e]));
             const int g1 = __float2int_rn(__uint_as_float(r[1][e]) * 256.0f);
             const int g2 = __float2int_rn(__uint_as_float(r[2][e]) * 65536.0f);
             const int g3 = __float2int_rn(__uint_as_float(r[3][e]) * 16777216.0f);
             const long long v = (long long)(g0 * 256 + g1) * 65536 + (long long)g2 * 256 + g3;
-            acc[j * 16 + e] += (unsigned long long)v << extra;
+            acc[j * EPI_STEP + e] += (unsigned long long)v << extra;
           }
         }
         sm100::tc_fence_before();
@@ -374,8 +380,8 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
       }
       const int z = kb0 / p.kb_per_split;
 #pragma unroll
-      for (int j = 0; j < 48; ++j) {
-        const int col = n0 + half * 48 + j;
+      for (int j = 0; j < EPI_COLS; ++j) {
+        const int col = n0 + cg * EPI_COLS + j;
         if (row < p.M && col < p.N) {
           const int E = ea + p.eb[col] - 14 - 8 * (NEXACT - 1) - p.sh;
           const double v = make_double((long long)acc[j], E);
