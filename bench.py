@@ -248,10 +248,11 @@ def run_ours(args, ws, rank, local):
 
 
 NDIG_PRODUCTS = 21     # digit products of the split-precision GEMM (6 digits, s + t <= 5)
-# DRAM bytes per (L, mu) row of the half-transform kernel (K = Nao = 1200, 192 columns), from one
-# ncu capture of the same kernel on 131072 rows (profiles/k_ozaki_m131072_k1200_n192.md), scaled
-# to a full launch by the rows it processes (the traffic is proportional to the rows).
-S1_TRAFFIC_PER_ROW = (1.937758e9 + 0.206009e9) / 131072
+# DRAM bytes per (L, mu) row of the half-transform kernel (K = Nao = 1200, 176 columns), from one
+# ncu capture of the same launch on the first 200 auxiliary functions (200 x 1200 rows;
+# profiles/k_ozaki_half_transform_nao1200_naux200.md), scaled to a full launch by the rows it
+# processes (the traffic is proportional to the rows: digits of B read once, H written once).
+S1_TRAFFIC_PER_ROW = (3.535900e9 + 0.386882e9) / (200 * 1200)
 
 
 def roofline_for(prec, r, work, peaks, s):
@@ -355,9 +356,17 @@ def main():
     ap.add_argument("--fp64-warmup", type=int, default=3)
     ap.add_argument("--cpu-rows", type=int, default=240)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-naux", type=int, default=None, metavar="N",
+                    help="profiling only: the same system with its first N auxiliary functions "
+                         "(a few GB on the device, for ncu captures); not a bench line")
     ap.add_argument("--split-gemm", default=None, metavar="M,K,N",
                     help="time only the emulated-FP64 GEMM on random M x K and K x N inputs")
     args = ap.parse_args()
+    if args.profile_naux:
+        global WORKLOAD
+        WORKLOAD = dict(WORKLOAD, naux=args.profile_naux,
+                        config=WORKLOAD["config"] + "_profile_naux%d" % args.profile_naux)
+        args.no_cpu_baseline = True
     if args.split_gemm:
         split_gemm_probe(args.split_gemm, args.steps, args.warmup)
         return
@@ -379,7 +388,7 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-                "config": {"workload": WORKLOAD["config"], "nao": 1200, "naux": 4800,
+                "config": {"workload": WORKLOAD["config"], "nao": WORKLOAD["nao"], "naux": WORKLOAD["naux"],
                            "ncore": 150, "active": "(22e,40o) as 5x8 orbitals"},
                 "cpu_baseline": {"value": v, "unit": "evals/s", "cores": vals[0]["cores"],
                                  "kind": "oracle", "sample": vals[0]["sample"]},
@@ -424,7 +433,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if primary == "fp64" else "bf16-digits->f64",
             "data": "synthetic (seeded counter-based generator; shapes of the paper's systems)",
-            "config": {"workload": WORKLOAD["config"], "nao": 1200, "naux": 4800, "ncore": 150,
+            "config": {"workload": WORKLOAD["config"], "nao": WORKLOAD["nao"], "naux": WORKLOAD["naux"], "ncore": 150,
                        "active": "(22e,40o) as (6e,8o)+4x(4e,8o)", "precision": primary,
                        "l2": "no flush: resident inputs (27.7 GB B) far exceed L2",
                        "parallelism": f"{ws} independent system(s), one per GPU"},
