@@ -14,8 +14,8 @@ products (a library primitive) as the only building block beyond plain loops:
   host-memory budget).
 * JK call, Eqs. J_1, J_2, K_1, K_2:  v_P = b^P_ij D_ij ; J_ij = v_P b^P_ij ;
   v^P_ik = b^P_ij gamma_jk ; K_ij = v^P_ik b^P_jk.
-* AO2MO, Eqs. ao2mo_1, ao2mo_2, ppaa:  b^P_{e p} = b^P_{ee} M ; b^P_{pp} = b^P_{ep} M ;
-  g^{pa}_{pa} = b^P_{pp} b^P_{aa}.
+* AO2MO, Eqs. ao2mo_1, ao2mo_2, ppaa, papa:  b^P_{e p} = b^P_{ee} M ; b^P_{pp} = b^P_{ep} M ;
+  g^{pa}_{pa} = b^P_{pp} b^P_{aa} ; g^{pp}_{aa} = b^P_{pa} b^P_{pa}.
 * LAS wave function, Eq. las_wfn: a product of fragment CAS states and a closed-shell core
   determinant.  Its active RDMs are the block products of the fragment RDMs (intra-fragment
   blocks, inter-fragment Coulomb D^K D^L and exchange -sum_sigma gamma^K_sigma gamma^L_sigma).
@@ -127,6 +127,32 @@ def df_transform(Bp: np.ndarray, n: int, C: np.ndarray, act: tuple[int, int],
         lmu[l0:l1] = b @ C_a
         lpu[l0:l1] = np.einsum("mp,Pmu->Ppu", C[:, p0:p1], lmu[l0:l1], optimize=True)
     return lmu, lpu
+
+
+def frag_ao2mo(Bp: np.ndarray, n: int, M: np.ndarray, a0: int, ma: int
+               ) -> tuple[np.ndarray, np.ndarray]:
+    """Fragment-embedding AO2MO, Eqs. ao2mo_1, ao2mo_2, ppaa and papa, in the basis the
+    Cholesky vectors are given in (the fragment's embedded orbitals e).
+
+    b^P_{e2 p1} = b^P_{e1 e2} M_{e1 p1} (Eq. ao2mo_1); b^P_{p1 p2} = b^P_{e2 p1} M_{e2 p2}
+    (Eq. ao2mo_2); with the active orbitals a = columns [a0, a0+ma) of M,
+    ppaa[p1, p2, a1, a2] = b^P_{p1 p2} b^P_{a1 a2} (Eq. ppaa) and
+    papa[p1, a1, p2, a2] = b^P_{p1 a1} b^P_{p2 a2} (Eq. papa), summed over P block by block.
+    Returns (ppaa [nmo][nmo][ma][ma], papa [nmo][ma][nmo][ma]) with nmo = M.shape[1]."""
+    nmo = M.shape[1]
+    act = slice(a0, a0 + ma)
+    ppaa = np.zeros((nmo, nmo, ma, ma))
+    papa = np.zeros((nmo, ma, nmo, ma))
+    for _, _, b in p_blocks(Bp, n):
+        nb = b.shape[0]
+        bep = b @ M                                                   # Eq. ao2mo_1
+        bpp = np.einsum("ep,Peq->Ppq", M, bep, optimize=True)         # Eq. ao2mo_2
+        baa = bpp[:, act, act]
+        ppaa += (bpp.reshape(nb, nmo * nmo).T @ baa.reshape(nb, ma * ma)
+                 ).reshape(nmo, nmo, ma, ma)                          # Eq. ppaa
+        bpa = bpp[:, :, act].reshape(nb, nmo * ma)
+        papa += (bpa.T @ bpa).reshape(nmo, ma, nmo, ma)               # Eq. papa
+    return ppaa, papa
 
 
 # ----------------------------------------------------------------------------------------

@@ -128,6 +128,43 @@ def test_df_transform_matches_mo_integrals(cfg0):
     assert np.abs(pu_vw - full[:, a0:a1, a0:a1, a0:a1]).max() < 1e-11
 
 
+def _frag_case():
+    # a non-orthogonal embedded-orbital matrix M (the transform need not be unitary)
+    s = make_system(9, 26, 2, [(2, 2)], seed=31)
+    rng = np.random.default_rng(7)
+    M = rng.standard_normal((s.nao, s.nao))
+    return s, M, 3, 3
+
+
+def test_frag_ao2mo_brute_force():
+    """Eqs. ao2mo_1..papa against the 4-index AO integrals transformed index by index."""
+    s, M, a0, ma = _frag_case()
+    ppaa, papa = O.frag_ao2mo(s.Bp, s.nao, M, a0, ma)
+    eri = np.einsum("mnls,mp,nq,lr,st->pqrt", O.ao_eri(s.Bp, s.nao), M, M, M, M)
+    act = slice(a0, a0 + ma)
+    assert np.abs(ppaa - eri[:, :, act, act]).max() < 1e-10 * np.abs(eri).max()
+    assert np.abs(papa - eri[:, act, :, act]).max() < 1e-10 * np.abs(eri).max()
+
+
+def test_frag_ao2mo_symmetry_and_consistency():
+    s, M, a0, ma = _frag_case()
+    ppaa, papa = O.frag_ao2mo(s.Bp, s.nao, M, a0, ma)
+    act = slice(a0, a0 + ma)
+    tol = 1e-12 * np.abs(ppaa).max()
+    assert np.abs(ppaa - ppaa.transpose(1, 0, 2, 3)).max() < tol
+    assert np.abs(ppaa - ppaa.transpose(0, 1, 3, 2)).max() < tol
+    assert np.abs(papa - papa.transpose(2, 3, 0, 1)).max() < tol
+    # (P a_k|a_i a_j) appears in both outputs
+    assert np.abs(ppaa[:, act, :, :] - papa[:, :, act, :]).max() < tol
+    # (pa|pa) from the half/full transform of Eqs. ao2mo_1-ao2mo_2 written the other way round
+    _, lpu = O.df_transform(s.Bp, s.nao, M, (a0, a0 + ma), 0, s.nao)
+    assert np.abs(np.einsum("Lpu,Lqv->puqv", lpu, lpu) - papa).max() < tol
+    # a transposed M (a plausible slip) fails the brute-force pin
+    bad, _ = O.frag_ao2mo(s.Bp, s.nao, np.ascontiguousarray(M.T), a0, ma)
+    eri = np.einsum("mnls,mp,nq,lr,st->pqrt", O.ao_eri(s.Bp, s.nao), M, M, M, M)
+    assert np.abs(bad - eri[:, :, act, act]).max() > 1e-3 * np.abs(eri).max()
+
+
 @pytest.mark.parametrize("which", ["cfg0", "small3"])
 def test_energy_three_ways(which, request):
     s = request.getfixturevalue(which)
