@@ -107,6 +107,19 @@ las_status las_df_jk(las_ctx* ctx, const double* C, double* J, double* K);
 las_status las_df_jk_density(las_ctx* ctx, const double* Cx, const double* w, int r, double* J,
                              double* K);
 
+/* Fragment-embedding AO2MO of a CASSCF subproblem (Eqs. ao2mo_1, ao2mo_2, ppaa, papa): the
+ * context holds the Cholesky vectors b^P_{e e'} in the fragment's embedded basis e (create it
+ * with nao = nmo = the number of embedded orbitals, any ncore/fragments), M holds the embedded
+ * MO coefficients and the active orbitals are its columns [a0, a0 + ma):
+ *   b^P_{e2 p1} = b^P_{e1 e2} M[e1][p1],   b^P_{p1 p2} = b^P_{e2 p1} M[e2][p2],
+ *   ppaa[p1][p2][a1][a2] = sum_P b^P_{p1 p2} b^P_{a0+a1, a0+a2}            (nmo x nmo x ma x ma)
+ *   papa[p1][a1][p2][a2] = sum_P b^P_{p1, a0+a1} b^P_{p2, a0+a2}          (nmo x ma x nmo x ma)
+ * M: device [nao][nmo] row-major; ppaa, papa: device, row-major as shown; either may be NULL.
+ * The first call allocates the call's own workspace (kept by the context until las_destroy);
+ * the auxiliary index is processed in chunks that fit the context's workspace cap. */
+las_status las_frag_ao2mo(las_ctx* ctx, const double* M, int a0, int ma, double* ppaa,
+                          double* papa);
+
 /* LAS energy.  h: device [nao][nao] one-electron Hamiltonian (symmetric).
  * dm1s: device, per fragment K the spin-separated 1-RDM [2][m_K][m_K] (alpha, beta),
  *       concatenated over fragments.

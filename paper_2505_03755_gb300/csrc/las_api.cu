@@ -72,6 +72,11 @@ struct las_ctx {
   size_t bytes;
   // split-precision state (owned)
   SplitState* split;
+  // fragment AO2MO workspace (allocated by the first las_frag_ao2mo call)
+  double *fH, *fT, *fpart;
+  long fLc, fpart_elems;
+  int fnmo, fma;
+  FragSplit* fsplit;
   // timing: a ring of LAS_TIMING_RING evaluations x 6 stage marks, read without per-call syncs
   int timing;
   cudaEvent_t* ev;       // [LAS_TIMING_RING][6]
@@ -112,6 +117,9 @@ static void free_all(las_ctx* x) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (x->split) split_destroy(x->split);
+  if (x->fsplit) frag_split_destroy(x->fsplit);
+  for (double* q : {x->fH, x->fT, x->fpart})
+    if (q) cudaFree(q);
   if (x->ev) {
     for (int i = 0; i < LAS_TIMING_RING * LAS_MARKS; ++i)
       if (x->ev[i]) cudaEventDestroy(x->ev[i]);
@@ -600,6 +608,129 @@ extern "C" las_status las_df_transform(las_ctx* x, const double* C, int p0, int 
     if ((st = check_launch()) != LAS_OK) return st;
   }
   return LAS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Fragment-embedding AO2MO (Eqs. ao2mo_1, ao2mo_2, ppaa, papa)
+// ------------------------------------------------------------------------------------------
+// Operand loaders of the two integral products over the chunk's T[L][p][q] (nmo x nmo per L)
+struct ActBlockB {   // (b, k = L, c = (u, v)) -> T[L][a0+u][a0+v]
+  const double* T;
+  long n2;
+  int nmo, a0, ma;
+  __device__ __forceinline__ double operator()(int, int k, int c) const {
+    const int u = c / ma, v = c - u * ma;
+    return T[(long)k * n2 + (long)(a0 + u) * nmo + a0 + v];
+  }
+};
+struct PActA {       // (b, r = (p, u), k = L) -> T[L][p][a0+u]
+  const double* T;
+  long n2;
+  int nmo, a0, ma;
+  __device__ __forceinline__ double operator()(int, int r, int k) const {
+    const int p = r / ma, u = r - p * ma;
+    return T[(long)k * n2 + (long)p * nmo + a0 + u];
+  }
+};
+struct PActB {       // (b, k = L, c = (q, v)) -> T[L][q][a0+v]
+  PActA a;
+  __device__ __forceinline__ double operator()(int b, int k, int c) const { return a(b, c, k); }
+};
+
+// Workspace of the fragment AO2MO: H [Lc][nmo][n] and T [Lc][nmo][nmo] per chunk of Lc
+// auxiliary rows, split-K partials of the two products, and (split mode) the digit planes.
+static las_status frag_workspace(las_ctx* x, int ma) {
+  const int n = x->n, nmo = x->nmo;
+  const long n2 = (long)nmo * nmo, m = (long)nmo * ma;
+  const long part = 8 * std::max(n2 * ma * ma, m * m);   // up to 8 K splits
+  const size_t per_aux = (size_t)8 * ((size_t)nmo * n + n2) +
+                         (x->prec == LAS_SPLIT_BF16 ? (size_t)12 * ((size_t)nmo * n + n2 + m) : 0);
+  const size_t fixed = (size_t)8 * part + (size_t)12 * nmo * n;
+  int Lc = x->X;
+  while (Lc > 1 && fixed + per_aux * Lc > x->ws_cap) Lc = (Lc + 1) / 2;
+  if (fixed + per_aux * Lc > x->ws_cap) return LAS_ERR_WORKSPACE;
+  const bool fits = x->fH && x->fnmo == nmo && x->fma >= ma && x->fLc >= Lc &&
+                    x->fpart_elems >= part &&
+                    (x->prec != LAS_SPLIT_BF16 || frag_split_fits(x->fsplit, n, nmo, ma, Lc));
+  if (fits) return LAS_OK;
+  LAS_CUDA_TRY(cudaStreamSynchronize(x->stream));
+  for (double** q : {&x->fH, &x->fT, &x->fpart}) {
+    if (*q) cudaFree(*q);
+    *q = nullptr;
+  }
+  if (x->fsplit) frag_split_destroy(x->fsplit);
+  x->fsplit = nullptr;
+  las_status st = LAS_OK;
+  if ((st = dalloc(x, (void**)&x->fH, sizeof(double) * (size_t)Lc * nmo * n)) != LAS_OK ||
+      (st = dalloc(x, (void**)&x->fT, sizeof(double) * (size_t)Lc * n2)) != LAS_OK ||
+      (st = dalloc(x, (void**)&x->fpart, sizeof(double) * (size_t)part)) != LAS_OK)
+    return st;
+  if (x->prec == LAS_SPLIT_BF16 &&
+      (st = frag_split_create(&x->fsplit, n, nmo, ma, Lc, x->stream, &x->bytes)) != LAS_OK)
+    return st;
+  x->fLc = Lc;
+  x->fnmo = nmo;
+  x->fma = ma;
+  x->fpart_elems = part;
+  return LAS_OK;
+}
+
+extern "C" las_status las_frag_ao2mo(las_ctx* x, const double* M, int a0, int ma, double* ppaa,
+                                     double* papa) {
+  if (!x || !M) return LAS_ERR_ARG;
+  if (ma < 1 || a0 < 0 || a0 + ma > x->nmo) return LAS_ERR_ARG;
+  if (!ppaa && !papa) return LAS_OK;
+  las_status st = frag_workspace(x, ma);
+  if (st != LAS_OK) return st;
+  const int n = x->n, nmo = x->nmo;
+  const long n2 = (long)nmo * nmo, m = (long)nmo * ma;
+  const bool split = x->prec == LAS_SPLIT_BF16;
+  if (split && (st = frag_split_prepare_M(x->fsplit, M, x->stream)) != LAS_OK) return st;
+  for (int l0 = 0; l0 < x->X; l0 += (int)x->fLc) {
+    const int nL = (int)std::min<long>(x->fLc, x->X - l0);
+    if (split) {
+      st = frag_split_chunk(x->split, x->fsplit, l0, nL, x->fH, x->fT, a0, ma, ppaa, papa,
+                            x->fpart, x->fpart_elems, l0 > 0, x->stream);
+      if (st != LAS_OK) return st;
+    } else {
+      // Eq. ao2mo_1: H[L][p][e2] = sum_e1 b^L(e2, e1) M[e1][p]
+      PackedSymA A{x->Bp, x->npair, l0};
+      StridedA Bm{M, 0, nmo, 1};
+      StridedC Ch{x->fH, (long)nmo * n, 1, n, 1.0, 0};
+      gemm_f64(n, nmo, n, nL, 1, A, Bm, Ch, x->stream);
+      // Eq. ao2mo_2: T[L][p][q] = sum_e H[L][p][e] M[e][q]
+      StridedA Ah{x->fH, (long)nmo * n, n, 1};
+      StridedC Ct{x->fT, n2, nmo, 1, 1.0, 0};
+      gemm_f64(nmo, nmo, n, nL, 1, Ah, Bm, Ct, x->stream);
+      if (ppaa) {
+        // Eq. ppaa: ppaa[(p,q)][(u,v)] (+)= sum_L T[L][(p,q)] T[L][a0+u][a0+v]
+        const long out = n2 * ma * ma;
+        const int tiles = (int)(((n2 + 63) / 64) * ((ma * ma + 63) / 64));
+        const int ks = (int)std::max(1L, std::min({8L, (2L * 152 + tiles - 1) / tiles,
+                                                   (long)nL / 64, x->fpart_elems / out}));
+        StridedA At{x->fT, 0, 1, n2};
+        ActBlockB Bt{x->fT, n2, nmo, a0, ma};
+        StridedC Cp{x->fpart, out, (long)ma * ma, 1, 1.0, 0};
+        gemm_f64((int)n2, ma * ma, nL, 1, ks, At, Bt, Cp, x->stream);
+        launch_reduce_partials(x->fpart, ks, out, ppaa, l0 > 0, x->stream);
+      }
+      if (papa) {
+        // Eq. papa: papa[(p,u)][(q,v)] (+)= sum_L T[L][p][a0+u] T[L][q][a0+v]
+        const long out = m * m;
+        const int tiles = (int)(((m + 63) / 64) * ((m + 63) / 64));
+        const int ks = (int)std::max(1L, std::min({8L, (2L * 152 + tiles - 1) / tiles,
+                                                   (long)nL / 64, x->fpart_elems / out}));
+        PActA Ap{x->fT, n2, nmo, a0, ma};
+        PActB Bp2{Ap};
+        StridedC Cp{x->fpart, out, m, 1, 1.0, 0};
+        gemm_f64((int)m, (int)m, nL, 1, ks, Ap, Bp2, Cp, x->stream);
+        launch_reduce_partials(x->fpart, ks, out, papa, l0 > 0, x->stream);
+      }
+    }
+    if ((st = check_launch()) != LAS_OK) return st;
+  }
+  if (split && papa) launch_mirror_lower(papa, (int)m, x->stream);
+  return check_launch();
 }
 
 // ------------------------------------------------------------------------------------------

@@ -643,23 +643,26 @@ k_colmax(const double* __restrict__ Ht, long R, int n, long seg, unsigned long l
 }
 
 // Digits of H^T scaled per row mu (exponents from the column maxima): HdT[s](mu, k) for the
-// rows k = (L,p) of Ht, transposed through shared memory.  Block: 32 rows k x all mu.
+// rows k = (L,p) of Ht, transposed through shared memory.  Block: 32 rows k x the columns
+// [blockIdx.y*COLS_PER_BLOCK, ...) of mu.
+constexpr int COLS_PER_BLOCK = 2048;
 __global__ void __launch_bounds__(256)
 k_slice_ht_cols(const double* __restrict__ Ht, long R, int n, const unsigned long long* mx,
                 Planes HdT, int* __restrict__ ex) {
   __shared__ __nv_bfloat16 tile[NDIG][32][34];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long r0 = (long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * COLS_PER_BLOCK, c1 = min(n, c0 + COLS_PER_BLOCK);
   if (blockIdx.x == 0)
-    for (int mu = threadIdx.x; mu < n; mu += 256) ex[mu] = exp_of_maxbits(mx[mu]);
-  for (int k0 = 0; k0 < n; k0 += 32) {
+    for (int mu = c0 + threadIdx.x; mu < c1; mu += 256) ex[mu] = exp_of_maxbits(mx[mu]);
+  for (int k0 = c0; k0 < c1; k0 += 32) {
     const int mu = k0 + lane;
-    const int e = mu < n ? exp_of_maxbits(mx[mu]) : 0;
+    const int e = mu < c1 ? exp_of_maxbits(mx[mu]) : 0;
     for (int i = 0; i < 4; ++i) {
       const int row = warp + 8 * i;
       const long r = r0 + row;
       __nv_bfloat16 d[NDIG];
-      digits_of((r < R && mu < n) ? Ht[r * n + mu] : 0.0, e, d);
+      digits_of((r < R && mu < c1) ? Ht[r * n + mu] : 0.0, e, d);
 #pragma unroll
       for (int s = 0; s < NDIG; ++s) tile[s][row][lane] = d[s];
     }
@@ -668,7 +671,7 @@ k_slice_ht_cols(const double* __restrict__ Ht, long R, int n, const unsigned lon
       const int kk = warp * 4 + i;
       const int m2 = k0 + kk;
       const long r = r0 + lane;
-      if (m2 < n && r < HdT.nkb * BK) {
+      if (m2 < c1 && r < HdT.nkb * BK) {
 #pragma unroll
         for (int s = 0; s < NDIG; ++s) HdT.p[HdT.idx(s, m2, r)] = tile[s][lane][kk];
       }
@@ -1057,7 +1060,8 @@ las_status split_exchange(SplitState* s, int nL, int oc, const double* Ht, doubl
     dim3 g1((unsigned)((n + 255) / 256), (unsigned)((R + seg - 1) / seg));
     k_colmax<<<g1, 256, 0, st>>>(Ht, R, (int)n, seg, s->mx);
     las_count_launch();
-    k_slice_ht_cols<<<(unsigned)((R + 31) / 32), 256, 0, st>>>(Ht, R, (int)n, s->mx, HT, s->hexp);
+    dim3 g2((unsigned)((R + 31) / 32), (unsigned)((n + COLS_PER_BLOCK - 1) / COLS_PER_BLOCK));
+    k_slice_ht_cols<<<g2, 256, 0, st>>>(Ht, R, (int)n, s->mx, HT, s->hexp);
     las_count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -1141,6 +1145,183 @@ extern "C" las_status las_split_gemm(long M, long N, long K, const double* A, lo
   LAS_CUDA_TRY(cudaMemcpyAsync(&h, status, 4, cudaMemcpyDeviceToHost, st));
   LAS_CUDA_TRY(cudaStreamSynchronize(st));
   return h ? (las_status)h : LAS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Fragment-embedding AO2MO in split precision (Eqs. ao2mo_1, ao2mo_2, ppaa, papa)
+// ------------------------------------------------------------------------------------------
+namespace lasdf_split {
+// Row (u, v) of the active block of T (rows (L, p), columns q), K = the auxiliary row L:
+// T[L][a0+u][a0+v]
+struct RowsAA {
+  const double* T;
+  long n2;
+  int nmo, a0, ma;
+  __device__ __forceinline__ double operator()(long r, long k) const {
+    const int u = (int)(r / ma), v = (int)(r - (long)u * ma);
+    return T[k * n2 + (long)(a0 + u) * nmo + a0 + v];
+  }
+};
+// Row (p, u) of the MO-active columns of T, K = L: T[L][p][a0+u]
+struct RowsPA {
+  const double* T;
+  long n2;
+  int nmo, a0, ma;
+  __device__ __forceinline__ double operator()(long r, long k) const {
+    const long p = r / ma, u = r - p * ma;
+    return T[k * n2 + p * nmo + a0 + u];
+  }
+};
+}  // namespace lasdf_split
+
+struct FragSplit {
+  int n, nmo, ma, Lc;
+  Planes Mdig;   int* Mexp;     // rows p of M^T, K = e
+  Planes Hd;     int* Hexp;     // rows (L, p) of the half transform, K = e
+  Planes Tpl;    int* Texp;     // rows (p, q) of T, K = L
+  Planes Taa;    int* Taaexp;   // rows (u, v) of the active block, K = L
+  Planes Tpa;    int* Tpaexp;   // rows (p, u), K = L
+  unsigned long long* mx;       // [nmo^2] column maxima of T
+  void* blob;
+};
+
+las_status frag_split_create(FragSplit** out, int n, int nmo, int ma, int Lc, cudaStream_t st,
+                             size_t* bytes) {
+  *out = nullptr;
+  if (!encode_fn()) return LAS_ERR_UNSUPPORTED;
+  if (ozaki_prepare() != LAS_OK) return LAS_ERR_CUDA;
+  FragSplit* f = (FragSplit*)calloc(1, sizeof(FragSplit));
+  if (!f) return LAS_ERR_INTERNAL;
+  f->n = n;
+  f->nmo = nmo;
+  f->ma = ma;
+  f->Lc = Lc;
+  const long n2 = (long)nmo * nmo, R1 = (long)Lc * nmo;
+  const size_t parts[] = {planes_bytes(nmo, n),          rup((size_t)nmo * 4, 256),
+                          planes_bytes(R1, n),           rup((size_t)R1 * 4, 256),
+                          planes_bytes(n2, Lc),          rup((size_t)n2 * 4, 256),
+                          planes_bytes((long)ma * ma, Lc), rup((size_t)ma * ma * 4, 256),
+                          planes_bytes((long)nmo * ma, Lc), rup((size_t)nmo * ma * 4, 256),
+                          (size_t)n2 * 8};
+  size_t total = 0;
+  for (size_t b : parts) total += rup(b, 256);
+  if (cudaMalloc(&f->blob, total) != cudaSuccess) {
+    las_record_cuda_error(cudaErrorMemoryAllocation, "cudaMalloc(frag ao2mo)", __FILE__, __LINE__);
+    free(f);
+    return LAS_ERR_CUDA;
+  }
+  // padding rows and K blocks are never written by the live-row slicers: zero them once
+  cudaError_t e = cudaMemsetAsync(f->blob, 0, total, st);
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "cudaMemsetAsync(frag ao2mo)", __FILE__, __LINE__);
+    cudaFree(f->blob);
+    free(f);
+    return LAS_ERR_CUDA;
+  }
+  uint8_t* w = (uint8_t*)f->blob;
+  auto take = [&](size_t b) { void* q = w; w += rup(b, 256); return q; };
+  f->Mdig = make_planes(take(parts[0]), nmo, n);
+  f->Mexp = (int*)take(parts[1]);
+  f->Hd = make_planes(take(parts[2]), R1, n);
+  f->Hexp = (int*)take(parts[3]);
+  f->Tpl = make_planes(take(parts[4]), n2, Lc);
+  f->Texp = (int*)take(parts[5]);
+  f->Taa = make_planes(take(parts[6]), (long)ma * ma, Lc);
+  f->Taaexp = (int*)take(parts[7]);
+  f->Tpa = make_planes(take(parts[8]), (long)nmo * ma, Lc);
+  f->Tpaexp = (int*)take(parts[9]);
+  f->mx = (unsigned long long*)take(parts[10]);
+  *bytes += total;
+  *out = f;
+  return LAS_OK;
+}
+
+void frag_split_destroy(FragSplit* f) {
+  if (!f) return;
+  if (f->blob) cudaFree(f->blob);
+  free(f);
+}
+
+int frag_split_fits(const FragSplit* f, int n, int nmo, int ma, int Lc) {
+  return f && f->n == n && f->nmo == nmo && f->ma >= ma && f->Lc >= Lc;
+}
+
+las_status frag_split_prepare_M(FragSplit* f, const double* M, cudaStream_t st) {
+  // rows p of M^T (K = e): element (p, e) = M[e][p]
+  return slice_rows(RowsStrided{M, 1, f->nmo, nullptr}, f->Mdig, f->Mexp, st, nullptr, true);
+}
+
+las_status frag_split_chunk(SplitState* s, FragSplit* f, int l0, int nL, double* H, double* T,
+                            int a0, int ma, double* ppaa, double* papa, double* part,
+                            long part_elems, int accumulate, cudaStream_t st) {
+  const int n = f->n, nmo = f->nmo;
+  const long n2 = (long)nmo * nmo, R1 = (long)nL * nmo;
+  if (nL < 1 || nL > f->Lc || ma > f->ma) return LAS_ERR_INTERNAL;
+  // Eq. ao2mo_1: H[L][p][e2] = sum_e1 b^L(e2, e1) M[e1][p]
+  las_status rc = ozaki_gemm(s->Bdig, (long)l0 * n, s->Bexp + (long)l0 * n, (long)nL * n, f->Mdig,
+                             0, f->Mexp, nmo, n, 1, 1, H, 0, 0, n, nmo, s->status, st);
+  // Eq. ao2mo_2: T[L][p][q] = sum_e H[L][p][e] M[e][q]
+  Planes Hd = f->Hd;
+  Hd.R = R1;
+  if (rc == LAS_OK) rc = slice_rows(RowsStrided{H, n, 1, nullptr}, Hd, f->Hexp, st, nullptr, true);
+  if (rc == LAS_OK)
+    rc = ozaki_gemm(Hd, 0, f->Hexp, R1, f->Mdig, 0, f->Mexp, nmo, n, 1, 0, T, nmo, 0, 0, 0,
+                    s->status, st);
+  if (rc != LAS_OK) return rc;
+  const long kb = (nL + BK - 1) / BK;
+  if (ppaa) {
+    // Eq. ppaa: ppaa[(p,q)][(u,v)] (+)= sum_L T[L][(p,q)] T[L][a0+u][a0+v]
+    Planes A = f->Tpl, B = f->Taa;
+    A.K = nL;
+    B.R = (long)ma * ma;
+    B.K = nL;
+    // rows (p,q) of T^T with per-row exponents: column maxima of T [nL][n2], then a transposing
+    // slicer (coalesced reads along (p,q))
+    cudaError_t e = cudaMemsetAsync(f->mx, 0, (size_t)n2 * 8, st);
+    if (e != cudaSuccess) {
+      las_record_cuda_error(e, "cudaMemsetAsync(frag colmax)", __FILE__, __LINE__);
+      return LAS_ERR_CUDA;
+    }
+    const long seg = 512;
+    dim3 g1((unsigned)((n2 + 255) / 256), (unsigned)((nL + seg - 1) / seg));
+    k_colmax<<<g1, 256, 0, st>>>(T, nL, (int)n2, seg, f->mx);
+    las_count_launch();
+    dim3 g2((unsigned)((nL + 31) / 32), (unsigned)((n2 + COLS_PER_BLOCK - 1) / COLS_PER_BLOCK));
+    k_slice_ht_cols<<<g2, 256, 0, st>>>(T, nL, (int)n2, f->mx, A, f->Texp);
+    las_count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      las_record_cuda_error(e, "frag slicer launch", __FILE__, __LINE__);
+      return LAS_ERR_CUDA;
+    }
+    if (rc == LAS_OK)
+      rc = slice_rows(RowsAA{T, n2, nmo, a0, ma}, B, f->Taaexp, st, nullptr, true);
+    const long out = n2 * ma * ma;
+    const int ks = balanced_ksplit(ozaki_tiles(n2, (long)ma * ma, 0), kb,
+                                   std::max(1L, std::min(kb, part_elems / out)));
+    if (rc == LAS_OK)
+      rc = ozaki_gemm(A, 0, f->Texp, n2, B, 0, f->Taaexp, (long)ma * ma, nL, ks, 0, part,
+                      (long)ma * ma, out, 0, 0, s->status, st);
+    if (rc != LAS_OK) return rc;
+    launch_reduce_partials(part, ks, out, ppaa, accumulate, st);
+  }
+  if (papa) {
+    // Eq. papa: papa[(p,u)][(q,v)] (+)= sum_L T[L][p][a0+u] T[L][q][a0+v] (lower triangle; the
+    // caller mirrors it once all chunks are in)
+    Planes A = f->Tpa;
+    A.R = (long)nmo * ma;
+    A.K = nL;
+    rc = slice_rows(RowsPA{T, n2, nmo, a0, ma}, A, f->Tpaexp, st, nullptr, true);
+    const long m = (long)nmo * ma, out = m * m;
+    const int ks = balanced_ksplit(ozaki_tiles(m, m, 1), kb,
+                                   std::max(1L, std::min(kb, part_elems / out)));
+    if (rc == LAS_OK)
+      rc = ozaki_gemm(A, 0, f->Tpaexp, m, A, 0, f->Tpaexp, m, nL, ks, 0, part, m, out, 0, 0,
+                      s->status, st, 1);
+    if (rc != LAS_OK) return rc;
+    launch_reduce_partials(part, ks, out, papa, accumulate, st);
+  }
+  return LAS_OK;
 }
 
 // ------------------------------------------------------------------------------------------

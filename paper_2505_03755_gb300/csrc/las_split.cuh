@@ -35,3 +35,18 @@ las_status split_one_electron(SplitState* s, const double* h, double* hC, double
 // Out (+)= sum_{(L,p)} H(mu,(L,p)) W((L,p),q) with Wt[q][(L,p)] = W_L(p,q) * 2^exp(L,p)
 las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, int accumulate,
                          cudaStream_t st);
+
+// Fragment-embedding AO2MO (Eqs. ao2mo_1, ao2mo_2, ppaa, papa) in split precision: digit planes
+// of M, of the chunk's half transform and of the slices of T that feed the two integral products.
+struct FragSplit;
+las_status frag_split_create(FragSplit** f, int n, int nmo, int ma, int Lc, cudaStream_t st,
+                             size_t* bytes);
+void frag_split_destroy(FragSplit* f);
+int frag_split_fits(const FragSplit* f, int n, int nmo, int ma, int Lc);
+las_status frag_split_prepare_M(FragSplit* f, const double* M, cudaStream_t st);
+// One chunk of auxiliary rows [l0, l0+nL): H [nL][nmo][n] and T [nL][nmo][nmo] are FP64
+// scratch; ppaa and papa are written (accumulate = 0) or accumulated; papa holds only its lower
+// triangle (as an (nmo*ma)^2 matrix) until the caller mirrors it.
+las_status frag_split_chunk(SplitState* s, FragSplit* f, int l0, int nL, double* H, double* T,
+                            int a0, int ma, double* ppaa, double* papa, double* part,
+                            long part_elems, int accumulate, cudaStream_t st);

@@ -79,6 +79,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.las_autotune.restype = i
     lib.las_df_jk_density.argtypes = [vp, vp, vp, i, vp, vp]
     lib.las_df_jk_density.restype = i
+    lib.las_frag_ao2mo.argtypes = [vp, vp, i, i, vp, vp]
+    lib.las_frag_ao2mo.restype = i
     lib.las_kernel_launches.argtypes = []
     lib.las_kernel_launches.restype = ctypes.c_long
     lib.las_status_str.argtypes = [i]
@@ -228,6 +230,20 @@ class LasDF:
         _check(self._lib.las_df_jk_density(self._h, _ptr(Cx), _ptr(w), int(Cx.shape[1]),
                                            _ptr(J), _ptr(K)), "las_df_jk_density")
         return J, K
+
+    def frag_ao2mo(self, M, a0: int, ma: int, want_ppaa: bool = True, want_papa: bool = True):
+        """Fragment-embedding AO2MO (Eqs. ao2mo_1, ao2mo_2, ppaa, papa) in this context's basis:
+        M (nao x nmo device float64) and the active columns [a0, a0+ma).  Returns (ppaa
+        [nmo][nmo][ma][ma], papa [nmo][ma][nmo][ma]); either may be skipped."""
+        import torch
+        nmo, dev = self.nmo, M.device
+        ppaa = torch.empty((nmo, nmo, ma, ma), dtype=torch.float64, device=dev) \
+            if want_ppaa else None
+        papa = torch.empty((nmo, ma, nmo, ma), dtype=torch.float64, device=dev) \
+            if want_papa else None
+        _check(self._lib.las_frag_ao2mo(self._h, _ptr(M), int(a0), int(ma), _ptr(ppaa),
+                                        _ptr(papa)), "las_frag_ao2mo")
+        return ppaa, papa
 
     def df_transform(self, C, p0: int, p1: int, want_lmu: bool = True, want_lpu: bool = True):
         import torch
