@@ -280,6 +280,48 @@ def roofline_for(prec, r, work, peaks, s):
     return None
 
 
+# One fragment's embedded CASSCF problem of the same system (Eqs. ao2mo_1-papa): 2 (8 + 240)
+# embedded orbitals (8 active and 1200/5 fragment orbitals, the paper's upper bound on the
+# embedded basis), the full auxiliary basis, the active orbitals in the middle of the MO range.
+AO2MO_WORKLOAD = dict(config="frag_ao2mo_nemb496_naux4800_act8", nemb=496, naux=4800, a0=244, ma=8)
+
+
+def run_ao2mo(local: int) -> dict:
+    """Time las_frag_ao2mo on AO2MO_WORKLOAD in both precisions (CUDA events on the library's
+    stream; ppaa and papa both produced)."""
+    import torch
+    from las_inputs import BASE_SEED, make_system
+    from paper_2505_03755_gb300 import LasDF
+    w = AO2MO_WORKLOAD
+    dev = torch.device(f"cuda:{local}")
+    s = make_system(w["nemb"], w["naux"], 16, [], seed=BASE_SEED + 5)
+    Bd = torch.from_numpy(s.Bp).to(dev)
+    s.Bp = None
+    M = torch.from_numpy(s.C).to(dev)
+    n, X, ma = w["nemb"], w["naux"], w["ma"]
+    flops = 2.0 * X * n ** 3 * 2 + 2.0 * X * n * n * ma * ma + 2.0 * X * (n * ma) ** 2
+    out = {"workload": w["config"], "fp64_equiv_flop": flops}
+    stream = torch.cuda.Stream(device=dev)
+    for prec, calls in (("split", 3), ("fp64", 1)):
+        las = LasDF(Bd, n, X, n, 16, [], precision=prec, stream=stream)
+        with torch.cuda.stream(stream):
+            las.frag_ao2mo(M, w["a0"], ma)
+            las.sync()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(calls):
+                las.frag_ao2mo(M, w["a0"], ma)
+            e1.record(stream)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1) / calls
+        las.close()
+        out[prec] = {"ms": ms, "calls": calls, "fp64_equiv_tflops": flops / (ms / 1e3) / 1e12}
+    del Bd
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(sample_rows: int):
     """The oracle as it stands, on auxiliary rows [0, sample_rows) of the same workload,
     scaled to a full evaluation."""
@@ -356,6 +398,8 @@ def main():
     ap.add_argument("--fp64-warmup", type=int, default=3)
     ap.add_argument("--cpu-rows", type=int, default=240)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ao2mo", action="store_true",
+                    help="skip the fragment-embedding AO2MO measurement")
     ap.add_argument("--profile-naux", type=int, default=None, metavar="N",
                     help="profiling only: the same system with its first N auxiliary functions "
                          "(a few GB on the device, for ncu captures); not a bench line")
@@ -367,6 +411,7 @@ def main():
         WORKLOAD = dict(WORKLOAD, naux=args.profile_naux,
                         config=WORKLOAD["config"] + "_profile_naux%d" % args.profile_naux)
         args.no_cpu_baseline = True
+        args.no_ao2mo = True
     if args.split_gemm:
         split_gemm_probe(args.split_gemm, args.steps, args.warmup)
         return
@@ -408,6 +453,8 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return
+    ao2mo = run_ao2mo(local) if (ws == 1 and not args.no_ao2mo and args.precision == "both") \
+        else None
     primary = "split" if ("split" in res and "error" not in res["split"]) else "fp64"
     r = res[primary]
     cpu = None
@@ -442,6 +489,7 @@ def main():
             "e2e": {"value": r["e2e_evals_per_s"], "unit": "evals/s",
                     "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
             "gpu_launches": r["launches"], "clocks": r["clocks"], "modes": modes,
+            "frag_ao2mo": ao2mo,
             "input_generation_s": tgen}
     print(json.dumps(line), flush=True)
     if ws > 1:
