@@ -14,6 +14,8 @@ products (a library primitive) as the only building block beyond plain loops:
   host-memory budget).
 * JK call, Eqs. J_1, J_2, K_1, K_2:  v_P = b^P_ij D_ij ; J_ij = v_P b^P_ij ;
   v^P_ik = b^P_ij gamma_jk ; K_ij = v^P_ik b^P_jk.
+* Effective potentials, Eqs. v_emb and vself:  v_sigma = J[D] - K[gamma_sigma], D = sum_sigma
+  gamma_sigma (in the AO basis, or in a fragment's embedded basis for the self potential).
 * AO2MO, Eqs. ao2mo_1, ao2mo_2, ppaa, papa:  b^P_{e p} = b^P_{ee} M ; b^P_{pp} = b^P_{ep} M ;
   g^{pa}_{pa} = b^P_{pp} b^P_{aa} ; g^{pp}_{aa} = b^P_{pa} b^P_{pa}.
 * LAS wave function, Eq. las_wfn: a product of fragment CAS states and a closed-shell core
@@ -153,6 +155,17 @@ def frag_ao2mo(Bp: np.ndarray, n: int, M: np.ndarray, a0: int, ma: int
         bpa = bpp[:, :, act].reshape(nb, nmo * ma)
         papa += (bpa.T @ bpa).reshape(nmo, ma, nmo, ma)               # Eq. papa
     return ppaa, papa
+
+
+def embedding_potentials(Bp: np.ndarray, n: int, gam_a: np.ndarray, gam_b: np.ndarray
+                         ) -> tuple[np.ndarray, np.ndarray]:
+    """Effective potentials of Eq. v_emb (or of Eq. vself when B and the densities are given in
+    a fragment's embedded basis): v_sigma = g^{..}_{..} D - g^{..}_{..} gamma_sigma, i.e.
+    v_sigma = J[gamma_alpha + gamma_beta] - K[gamma_sigma] with J and K of the JK call
+    (Eqs. J_1-K_2).  Returns (v_alpha, v_beta)."""
+    (J_a, J_b), (K_a, K_b) = df_jk(Bp, n, [gam_a, gam_b])
+    J = J_a + J_b
+    return J - K_a, J - K_b
 
 
 # ----------------------------------------------------------------------------------------

@@ -165,6 +165,55 @@ def test_frag_ao2mo_symmetry_and_consistency():
     assert np.abs(bad - eri[:, :, act, act]).max() > 1e-3 * np.abs(eri).max()
 
 
+def _spin_densities(s):
+    """gamma_sigma = C_c C_c^T + C_a gamma^act_sigma C_a^T of a LAS state (AO basis)."""
+    c, a = s.ncore, s.nactive
+    C_c, C_a = s.C[:, :c], s.C[:, c:c + a]
+    out = []
+    for sigma in range(2):
+        g = np.zeros((a, a))
+        off = 0
+        for d in s.dm1s:
+            m = d.shape[-1]
+            g[off:off + m, off:off + m] = d[sigma]
+            off += m
+        out.append(C_c @ C_c.T + C_a @ g @ C_a.T)
+    return out
+
+
+def test_embedding_potentials_brute_force(small3):
+    """Eq. v_emb with the 4-index integrals written out (open-shell fragment: gamma_a != gamma_b)."""
+    s = small3
+    ga, gb = _spin_densities(s)
+    assert np.abs(ga - gb).max() > 1e-3
+    va, vb = O.embedding_potentials(s.Bp, s.nao, ga, gb)
+    eri = O.ao_eri(s.Bp, s.nao)
+    D = ga + gb
+    for v, g in ((va, ga), (vb, gb)):
+        ref = np.einsum("mnls,ls->mn", eri, D) - np.einsum("mlsn,ls->mn", eri, g)
+        assert np.abs(v - ref).max() < 1e-11 * np.abs(ref).max()
+    # a plausible slip, the other spin's exchange, is caught
+    ref_a = np.einsum("mnls,ls->mn", eri, D) - np.einsum("mlsn,ls->mn", eri, ga)
+    assert np.abs(vb - ref_a).max() > 1e-6 * np.abs(ref_a).max()
+
+
+def test_embedding_potentials_match_fock_terms(small3):
+    """Closed-shell core alone: v_sigma = F^I - h; the LAS state: (v_a + v_b)/2 = F^I - h + F^A
+    (the Fock-like matrices of the pinned energy and gradient)."""
+    s = small3
+    r = O.system_energy_grad(s, with_grad=False)
+    C_c = s.C[:, :s.ncore]
+    gc = C_c @ C_c.T
+    va, vb = O.embedding_potentials(s.Bp, s.nao, gc, gc)
+    ref = r["FI"] - s.h
+    assert np.abs(va - ref).max() < 1e-11 * np.abs(ref).max()
+    assert np.abs(vb - ref).max() < 1e-11 * np.abs(ref).max()
+    ga, gb = _spin_densities(s)
+    va, vb = O.embedding_potentials(s.Bp, s.nao, ga, gb)
+    ref = r["FI"] - s.h + r["FA"]
+    assert np.abs(0.5 * (va + vb) - ref).max() < 1e-11 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("which", ["cfg0", "small3"])
 def test_energy_three_ways(which, request):
     s = request.getfixturevalue(which)
