@@ -120,6 +120,17 @@ las_status las_df_jk_density(las_ctx* ctx, const double* Cx, const double* w, in
 las_status las_frag_ao2mo(las_ctx* ctx, const double* M, int a0, int ma, double* ppaa,
                           double* papa);
 
+/* Effective potentials of Eq. v_emb (Eq. vself when the context holds a fragment's embedded-basis
+ * Cholesky vectors and the densities are the fragment's own), for spin densities in factored
+ * form gamma_sigma = C_sigma diag(w_sigma) C_sigma^T (C_sigma: device [nao][r_sigma], w_sigma:
+ * device [r_sigma]; either rank may be 0):
+ *   v_sigma = J[gamma_alpha + gamma_beta] - K[gamma_sigma]          (device [nao][nao] each)
+ * Two general-density JK calls (las_df_jk_density) and their combination; the same rank limit
+ * applies to r_alpha and r_beta. */
+las_status las_veff(las_ctx* ctx, const double* C_alpha, const double* w_alpha, int r_alpha,
+                    const double* C_beta, const double* w_beta, int r_beta, double* v_alpha,
+                    double* v_beta);
+
 /* LAS energy.  h: device [nao][nao] one-electron Hamiltonian (symmetric).
  * dm1s: device, per fragment K the spin-separated 1-RDM [2][m_K][m_K] (alpha, beta),
  *       concatenated over fragments.

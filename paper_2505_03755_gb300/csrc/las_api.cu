@@ -77,6 +77,7 @@ struct las_ctx {
   long fLc, fpart_elems;
   int fnmo, fma;
   FragSplit* fsplit;
+  double *vJ, *vK;   // scratch of las_veff (allocated by its first call)
   // timing: a ring of LAS_TIMING_RING evaluations x 6 stage marks, read without per-call syncs
   int timing;
   cudaEvent_t* ev;       // [LAS_TIMING_RING][6]
@@ -118,7 +119,7 @@ static void free_all(las_ctx* x) {
     if (p) cudaFree(p);
   if (x->split) split_destroy(x->split);
   if (x->fsplit) frag_split_destroy(x->fsplit);
-  for (double* q : {x->fH, x->fT, x->fpart})
+  for (double* q : {x->fH, x->fT, x->fpart, x->vJ, x->vK})
     if (q) cudaFree(q);
   if (x->ev) {
     for (int i = 0; i < LAS_TIMING_RING * LAS_MARKS; ++i)
@@ -608,6 +609,33 @@ extern "C" las_status las_df_transform(las_ctx* x, const double* C, int p0, int 
     if ((st = check_launch()) != LAS_OK) return st;
   }
   return LAS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Effective potentials (Eqs. v_emb, vself): v_sigma = J[gamma_a + gamma_b] - K[gamma_sigma]
+// ------------------------------------------------------------------------------------------
+extern "C" las_status las_veff(las_ctx* x, const double* Ca, const double* wa, int ra,
+                               const double* Cb, const double* wb, int rb, double* va,
+                               double* vb) {
+  if (!x || !va || !vb || ra < 0 || rb < 0) return LAS_ERR_ARG;
+  if ((ra > 0 && (!Ca || !wa)) || (rb > 0 && (!Cb || !wb))) return LAS_ERR_ARG;
+  if (ra > x->o || rb > x->o) return LAS_ERR_ARG;
+  const long nn = (long)x->n * x->n;
+  if (!x->vJ) {
+    las_status st = LAS_OK;
+    if ((st = dalloc(x, (void**)&x->vJ, sizeof(double) * nn)) != LAS_OK ||
+        (st = dalloc(x, (void**)&x->vK, sizeof(double) * nn)) != LAS_OK)
+      return st;
+  }
+  // alpha: va = J_a, vK = K_a;  beta: vJ = J_b, vb = K_b
+  las_status st = las_df_jk_density(x, Ca, wa, ra, va, x->vK);
+  if (st == LAS_OK) st = las_df_jk_density(x, Cb, wb, rb, x->vJ, vb);
+  if (st != LAS_OK) return st;
+  launch_axpy(va, x->vJ, 1.0, nn, x->stream);      // va = J[D]
+  launch_scale(vb, nn, -1.0, x->stream);
+  launch_axpy(vb, va, 1.0, nn, x->stream);         // vb = J[D] - K_b
+  launch_axpy(va, x->vK, -1.0, nn, x->stream);     // va = J[D] - K_a
+  return check_launch();
 }
 
 // ------------------------------------------------------------------------------------------

@@ -81,6 +81,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.las_df_jk_density.restype = i
     lib.las_frag_ao2mo.argtypes = [vp, vp, i, i, vp, vp]
     lib.las_frag_ao2mo.restype = i
+    lib.las_veff.argtypes = [vp, vp, vp, i, vp, vp, i, vp, vp]
+    lib.las_veff.restype = i
     lib.las_kernel_launches.argtypes = []
     lib.las_kernel_launches.restype = ctypes.c_long
     lib.las_status_str.argtypes = [i]
@@ -230,6 +232,18 @@ class LasDF:
         _check(self._lib.las_df_jk_density(self._h, _ptr(Cx), _ptr(w), int(Cx.shape[1]),
                                            _ptr(J), _ptr(K)), "las_df_jk_density")
         return J, K
+
+    def veff(self, C_alpha, w_alpha, C_beta, w_beta):
+        """Effective potentials v_sigma = J[gamma_a + gamma_b] - K[gamma_sigma] (Eqs. v_emb,
+        vself) of gamma_sigma = C_sigma diag(w_sigma) C_sigma^T (device float64 tensors)."""
+        import torch
+        n, dev = self.nao, C_alpha.device
+        va = torch.empty((n, n), dtype=torch.float64, device=dev)
+        vb = torch.empty((n, n), dtype=torch.float64, device=dev)
+        _check(self._lib.las_veff(self._h, _ptr(C_alpha), _ptr(w_alpha), int(C_alpha.shape[1]),
+                                  _ptr(C_beta), _ptr(w_beta), int(C_beta.shape[1]), _ptr(va),
+                                  _ptr(vb)), "las_veff")
+        return va, vb
 
     def frag_ao2mo(self, M, a0: int, ma: int, want_ppaa: bool = True, want_papa: bool = True):
         """Fragment-embedding AO2MO (Eqs. ao2mo_1, ao2mo_2, ppaa, papa) in this context's basis:
