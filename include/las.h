@@ -101,7 +101,9 @@ las_status las_df_jk(las_ctx* ctx, const double* C, double* J, double* K);
  *   D = sum_{k < r} w[k] Cx[:,k] Cx[:,k]^T     (Cx: device [nao][r] row-major, w: device [r]),
  * e.g. D = C_x M C_x^T after diagonalising M, or one spin density gamma_sigma of Eq. v_emb:
  *   J[mu][nu] = sum_L b^L_{mu nu} Tr(b^L D),   K[mu][nu] = sum_L (b^L D b^L)_{mu nu}.
- * Weights of either sign are allowed (D = D+ - D- is evaluated as two factored parts).
+ * Weights of either sign are allowed (D = D+ - D- is evaluated as two factored parts, each over
+ * the columns of its sign; zero weights are skipped).  The call reads the two column counts back
+ * to the host once (one synchronisation of the context's stream), so it is not graph-capturable.
  * Requires r <= ncore + sum(nact) of the context (create a JK context with ncore >= r and no
  * fragments for densities of other ranks).  J, K: device [nao][nao]; either may be NULL. */
 las_status las_df_jk_density(las_ctx* ctx, const double* Cx, const double* w, int r, double* J,

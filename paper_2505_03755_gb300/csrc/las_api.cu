@@ -78,6 +78,8 @@ struct las_ctx {
   int fnmo, fma;
   FragSplit* fsplit;
   double *vJ, *vK;   // scratch of las_veff (allocated by its first call)
+  int* widx;          // [2*o + 2] columns of each weight sign and their counts (JK density)
+  int wcount[2];      // host copy of those counts
   // timing: a ring of LAS_TIMING_RING evaluations x 6 stage marks, read without per-call syncs
   int timing;
   cudaEvent_t* ev;       // [LAS_TIMING_RING][6]
@@ -113,7 +115,7 @@ static las_status dalloc(las_ctx* x, void** p, size_t bytes) {
 
 static void free_all(las_ctx* x) {
   void* ptrs[] = {x->Cocc, x->Ht, x->T, x->W, x->part, x->Out, x->hC, x->hmo, x->M, x->eps,
-                  x->vc, x->va, x->Jp, x->Jt, x->Kt, x->status, x->dC, x->dh, x->ddm1, x->ddm2,
+                  x->vc, x->va, x->Jp, x->Jt, x->Kt, x->widx, x->status, x->dC, x->dh, x->ddm1, x->ddm2,
                   x->dE, x->dG};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -218,6 +220,7 @@ extern "C" las_status las_create(las_ctx** out, const las_dims* d, const double*
   ALLOC(Jp, x->npair);
   ALLOC(Jt, (size_t)x->n * x->n);
   ALLOC(Kt, (size_t)x->n * x->n);
+  ALLOC(widx, 2 * (size_t)x->o + 2);
   ALLOC(status, 4);
   ALLOC(dC, (size_t)x->n * x->nmo);
   ALLOC(dh, (size_t)x->n * x->n);
@@ -570,15 +573,30 @@ extern "C" las_status las_df_jk_density(las_ctx* x, const double* Cx, const doub
     if (K) LAS_CUDA_TRY(cudaMemsetAsync(K, 0, (size_t)n * n * 8, x->stream));
     return LAS_OK;
   }
-  // D = D+ - D-,  D± = sum_k max(±w_k, 0) c_k c_k^T
-  launch_pack_weighted(Cx, w, +1.0, n, r, x->op, x->Cocc, x->stream);
-  las_status st = jk_raw(x, r, J, K);
-  if (st != LAS_OK) return st;
-  launch_pack_weighted(Cx, w, -1.0, n, r, x->op, x->Cocc, x->stream);
-  st = jk_raw(x, r, J ? x->Jt : nullptr, K ? x->Kt : nullptr);
-  if (st != LAS_OK) return st;
-  if (J) launch_axpy(J, x->Jt, -1.0, (long)n * n, x->stream);
-  if (K) launch_axpy(K, x->Kt, -1.0, (long)n * n, x->stream);
+  // D = D+ - D-,  D± = sum_k max(±w_k, 0) c_k c_k^T, each over the columns of its sign only
+  // (their counts size the transforms, so they are read back once)
+  int* idx_pos = x->widx;
+  int* idx_neg = x->widx + x->o;
+  int* counts = x->widx + 2 * x->o;
+  launch_sign_split(w, r, idx_pos, idx_neg, counts, x->stream);
+  LAS_CUDA_TRY(cudaMemcpyAsync(x->wcount, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                               x->stream));
+  LAS_CUDA_TRY(cudaStreamSynchronize(x->stream));
+  const int rp = x->wcount[0], rn = x->wcount[1];
+  las_status st = LAS_OK;
+  if (rp > 0) {
+    launch_pack_weighted(Cx, w, idx_pos, rp, +1.0, n, r, x->op, x->Cocc, x->stream);
+    if ((st = jk_raw(x, rp, J, K)) != LAS_OK) return st;
+  } else {
+    if (J) LAS_CUDA_TRY(cudaMemsetAsync(J, 0, (size_t)n * n * 8, x->stream));
+    if (K) LAS_CUDA_TRY(cudaMemsetAsync(K, 0, (size_t)n * n * 8, x->stream));
+  }
+  if (rn > 0) {
+    launch_pack_weighted(Cx, w, idx_neg, rn, -1.0, n, r, x->op, x->Cocc, x->stream);
+    if ((st = jk_raw(x, rn, J ? x->Jt : nullptr, K ? x->Kt : nullptr)) != LAS_OK) return st;
+    if (J) launch_axpy(J, x->Jt, -1.0, (long)n * n, x->stream);
+    if (K) launch_axpy(K, x->Kt, -1.0, (long)n * n, x->stream);
+  }
   return check_launch();
 }
 

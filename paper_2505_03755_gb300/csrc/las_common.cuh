@@ -91,8 +91,11 @@ void launch_per_aux(const double* T, int nL, int op, const double* dm1s, const d
 void launch_scale(double* p, long count, double a, cudaStream_t s);
 void launch_mirror_lower(double* K, int n, cudaStream_t s);
 void launch_axpy(double* y, const double* x, double a, long count, cudaStream_t s);
-void launch_pack_weighted(const double* Cx, const double* w, double sign, int n, int r, int op,
-                          double* Cocc, cudaStream_t s);
+// Columns of each sign of w (k_sign_split), then the packed factor of one sign
+void launch_sign_split(const double* w, int r, int* idx_pos, int* idx_neg, int* counts,
+                       cudaStream_t s);
+void launch_pack_weighted(const double* Cx, const double* w, const int* idx, int cnt,
+                          double sign, int n, int r, int op, double* Cocc, cudaStream_t s);
 void launch_reduce_partials(const double* part, int nsplit, long count, double* out,
                             int accumulate, cudaStream_t s);
 void launch_assemble_grad(const double* Out, const double* hC, const double* dm1s,

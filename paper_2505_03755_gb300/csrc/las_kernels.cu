@@ -224,15 +224,30 @@ k_per_aux(const double* __restrict__ T, int nL, int op, const double* __restrict
 }
 
 // Cocc[mu][k] = Cx[mu][k] * sqrt(max(sign * w[k], 0)) for k < r, zero for r <= k < op
+// Columns of one sign of the weights, in order: idx[0..cnt) (sign = +1 or -1 picks w > 0 or w < 0).
+__global__ void k_sign_split(const double* __restrict__ w, int r, int* __restrict__ idx_pos,
+                             int* __restrict__ idx_neg, int* __restrict__ counts) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int np = 0, nn = 0;
+  for (int k = 0; k < r; ++k) {
+    if (w[k] > 0.0) idx_pos[np++] = k;
+    else if (w[k] < 0.0) idx_neg[nn++] = k;
+  }
+  counts[0] = np;
+  counts[1] = nn;
+}
+
+// Cocc[mu][j] = Cx[mu][idx[j]] * sqrt(sign * w[idx[j]]) for j < cnt, zero for cnt <= j < op
 __global__ void k_pack_weighted(const double* __restrict__ Cx, const double* __restrict__ w,
-                                double sign, int n, int r, int op, double* __restrict__ Cocc) {
+                                const int* __restrict__ idx, int cnt, double sign, int n, int r,
+                                int op, double* __restrict__ Cocc) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i >= (long)n * op) return;
-  const int mu = (int)(i / op), k = (int)(i % op);
+  const int mu = (int)(i / op), j = (int)(i % op);
   double v = 0.0;
-  if (k < r) {
-    const double wk = sign * w[k];
-    if (wk > 0.0) v = Cx[(long)mu * r + k] * sqrt(wk);
+  if (j < cnt) {
+    const int k = idx[j];
+    v = Cx[(long)mu * r + k] * sqrt(sign * w[k]);
   }
   Cocc[i] = v;
 }
@@ -424,9 +439,16 @@ void launch_per_aux(const double* T, int nL, int op, const double* dm1s, const d
   las_count_launch();
 }
 
-void launch_pack_weighted(const double* Cx, const double* w, double sign, int n, int r, int op,
-                          double* Cocc, cudaStream_t s) {
-  k_pack_weighted<<<nblk((long)n * op, 256), 256, 0, s>>>(Cx, w, sign, n, r, op, Cocc);
+void launch_sign_split(const double* w, int r, int* idx_pos, int* idx_neg, int* counts,
+                       cudaStream_t s) {
+  k_sign_split<<<1, 32, 0, s>>>(w, r, idx_pos, idx_neg, counts);
+  las_count_launch();
+}
+
+void launch_pack_weighted(const double* Cx, const double* w, const int* idx, int cnt,
+                          double sign, int n, int r, int op, double* Cocc, cudaStream_t s) {
+  k_pack_weighted<<<nblk((long)n * op, 256), 256, 0, s>>>(Cx, w, idx, cnt, sign, n, r, op,
+                                                         Cocc);
   las_count_launch();
 }
 
