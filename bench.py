@@ -356,6 +356,57 @@ def run_ao2mo(local: int) -> dict:
     return out
 
 
+def run_batched(local: int, reps: int = 5) -> dict:
+    """The 64-system uneven workload (Nao ~ U[100,600], Naux = 4 Nao, 2-6 fragments of 2-8
+    orbitals) in split precision: every system's evaluation under one captured CUDA graph,
+    replayed `reps` times (CUDA events on the replay stream).  Each context gets a 768 MiB
+    workspace cap so that the 64 contexts (52 GB of packed B, 159 GB of digit planes) fit."""
+    import torch
+    from las_inputs import batched_specs, make_system
+    from paper_2505_03755_gb300 import LasDF, energy_grad_batched
+    dev = torch.device(f"cuda:{local}")
+    stream = torch.cuda.Stream(device=dev)
+    las, items, bufs = [], [], []
+    t0 = time.perf_counter()
+    specs = batched_specs(64)
+    for sp in specs:
+        s = make_system(sp["nao"], sp["naux"], sp["ncore"], sp["frags"], sp["seed"])
+        Bd = torch.from_numpy(s.Bp).to(dev)
+        s.Bp = None
+        L = LasDF(Bd, s.nao, s.naux, s.nmo, s.ncore, s.nact, precision="split",
+                  max_workspace_bytes=768 << 20, stream=stream)
+        E = torch.empty((), dtype=torch.float64, device=dev)
+        G = torch.empty((s.nao, s.nmo), dtype=torch.float64, device=dev)
+        it = (torch.from_numpy(s.C).to(dev), torch.from_numpy(s.h).to(dev),
+              torch.from_numpy(s.dm1s_flat()).to(dev), torch.from_numpy(s.dm2_flat()).to(dev),
+              E, G)
+        las.append(L)
+        items.append(it)
+        bufs.append(Bd)
+    tgen = time.perf_counter() - t0
+    with torch.cuda.stream(stream):
+        for _ in range(2):                      # the first call captures the graph
+            energy_grad_batched(las, items, stream=stream)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            energy_grad_batched(las, items, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    dev_bytes = sum(L.device_bytes() for L in las)
+    for L in las:
+        L.close()
+    del bufs
+    torch.cuda.empty_cache()
+    return {"workload": "batched64_nao100-600_naux4nao", "systems": len(specs),
+            "precision": "split", "graph_replays": reps, "ms_per_batch": ms,
+            "evals_per_s": len(specs) / (ms / 1e3), "device_gb": dev_bytes / 1e9,
+            "input_generation_s": tgen}
+
+
 def cpu_baseline(sample_rows: int):
     """The oracle as it stands, on auxiliary rows [0, sample_rows) of the same workload,
     scaled to a full evaluation."""
@@ -434,6 +485,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ao2mo", action="store_true",
                     help="skip the fragment-embedding AO2MO measurement")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 64-system batched (captured graph) measurement")
     ap.add_argument("--profile-naux", type=int, default=None, metavar="N",
                     help="profiling only: the same system with its first N auxiliary functions "
                          "(a few GB on the device, for ncu captures); not a bench line")
@@ -446,6 +499,7 @@ def main():
                         config=WORKLOAD["config"] + "_profile_naux%d" % args.profile_naux)
         args.no_cpu_baseline = True
         args.no_ao2mo = True
+        args.no_batched = True
     if args.split_gemm:
         split_gemm_probe(args.split_gemm, args.steps, args.warmup)
         return
@@ -489,6 +543,8 @@ def main():
         return
     ao2mo = run_ao2mo(local) if (ws == 1 and not args.no_ao2mo and args.precision == "both") \
         else None
+    batched = run_batched(local) if (ws == 1 and not args.no_batched and
+                                     args.precision == "both") else None
     primary = "split" if ("split" in res and "error" not in res["split"]) else "fp64"
     r = res[primary]
     cpu = None
@@ -524,7 +580,7 @@ def main():
             "e2e": {"value": r["e2e_evals_per_s"], "unit": "evals/s",
                     "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
             "gpu_launches": r["launches"], "clocks": r["clocks"], "modes": modes,
-            "frag_ao2mo": ao2mo,
+            "frag_ao2mo": ao2mo, "batched": batched,
             "input_generation_s": tgen}
     print(json.dumps(line), flush=True)
     if ws > 1:

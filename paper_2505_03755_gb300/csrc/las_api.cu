@@ -809,26 +809,72 @@ extern "C" las_status las_energy_grad_batched(int nsys, las_ctx* const* ctxs,
       return LAS_OK;
     }
   }
-  // capture every system's chain, in order, on a private stream (the caller's stream may be the
-  // legacy default stream, which cannot be captured); the graph is then launched on `st`
-  static cudaStream_t cap_stream[64];
+  // capture the systems' chains on private streams (the caller's stream may be the legacy
+  // default stream, which cannot be captured): a fork into LAS_BRANCHES branch streams, each
+  // running its share of the systems in order, and a join, so that the chains of different
+  // systems overlap on the GPU (small systems' grids leave most SMs to the others); systems are
+  // shared out largest first to the branch with the least work so far; the graph is then
+  // launched on `st`
+  constexpr int LAS_BRANCHES = 8;
+  static cudaStream_t cap_stream[64], br_stream[64][LAS_BRANCHES];
+  static cudaEvent_t fork_ev[64], join_ev[64][LAS_BRANCHES];
   int dev = 0;
   LAS_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return LAS_ERR_UNSUPPORTED;
-  if (!cap_stream[dev]) LAS_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream[dev], cudaStreamNonBlocking));
+  if (!cap_stream[dev]) {
+    LAS_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream[dev], cudaStreamNonBlocking));
+    LAS_CUDA_TRY(cudaEventCreateWithFlags(&fork_ev[dev], cudaEventDisableTiming));
+    for (int b = 0; b < LAS_BRANCHES; ++b) {
+      LAS_CUDA_TRY(cudaStreamCreateWithFlags(&br_stream[dev][b], cudaStreamNonBlocking));
+      LAS_CUDA_TRY(cudaEventCreateWithFlags(&join_ev[dev][b], cudaEventDisableTiming));
+    }
+  }
   cudaStream_t cs = cap_stream[dev];
+  std::vector<int> order(nsys), branch(nsys);
+  for (int i = 0; i < nsys; ++i) order[i] = i;
+  auto cost = [&](int i) {   // the half transform's work: X n^2 op
+    return (double)ctxs[i]->X * ctxs[i]->n * ctxs[i]->n * ctxs[i]->op;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  const int nb = std::min(nsys, LAS_BRANCHES);
+  {
+    double load[LAS_BRANCHES] = {0};
+    for (int i : order) {
+      int b = 0;
+      for (int k = 1; k < nb; ++k)
+        if (load[k] < load[b]) b = k;
+      branch[i] = b;
+      load[b] += cost(i);
+    }
+  }
   LAS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   las_status rc = LAS_OK;
-  for (int i = 0; i < nsys && rc == LAS_OK; ++i) {
+  cudaError_t ce = cudaEventRecord(fork_ev[dev], cs);
+  for (int b = 0; b < nb && ce == cudaSuccess; ++b)
+    ce = cudaStreamWaitEvent(br_stream[dev][b], fork_ev[dev], 0);
+  if (ce != cudaSuccess) {
+    las_record_cuda_error(ce, "graph fork", __FILE__, __LINE__);
+    rc = LAS_ERR_CUDA;
+  }
+  for (int k = 0; k < nsys && rc == LAS_OK; ++k) {
+    const int i = order[k];
     las_ctx* x = ctxs[i];
     cudaStream_t saved = x->stream;
     const int timing = x->timing;
-    x->stream = cs;
+    x->stream = br_stream[dev][branch[i]];
     x->timing = 0;
     rc = evaluate(x, items[i].C, items[i].h, items[i].dm1s, items[i].dm2, items[i].E,
                   items[i].dEdC, nullptr);
     x->stream = saved;
     x->timing = timing;
+  }
+  for (int b = 0; b < nb && rc == LAS_OK; ++b) {
+    ce = cudaEventRecord(join_ev[dev][b], br_stream[dev][b]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, join_ev[dev][b], 0);
+    if (ce != cudaSuccess) {
+      las_record_cuda_error(ce, "graph join", __FILE__, __LINE__);
+      rc = LAS_ERR_CUDA;
+    }
   }
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &graph);
