@@ -561,19 +561,21 @@ k_digits_long(Acc acc, Planes P, long rows, long kbc, const unsigned long long* 
 }
 
 // Half-transformed rows (L,p) of Ht [R][n]: exponents, digit planes Hd (rows (L,p), K = mu) and
-// the same digits transposed, HdT (rows mu, K = (L,p)), in one pass.  Block: 32 rows r, 256
-// threads; per 64-column step each warp cuts 8 columns of all 32 rows (16-byte stores into Hd),
-// then 16-byte stores of 8 consecutive rows r into HdT from a transposed shared tile.  Rows of Hd
-// beyond the block's 32 and rows mu >= n of HdT are never written (they stay zero from set-up).
+// the same digits transposed, HdT (rows mu, K = (L,p)), in one pass.  Block: 16 rows r, 256
+// threads.  The row maxima are read first (warp per row); the digit pass then re-reads the
+// block's rows while they are still in L2: thread (r, c) cuts 8 consecutive columns of row r per
+// 128-column step (a warp's 16-byte stores into Hd cover 512 contiguous bytes), and the
+// transposed tile gives 32-byte stores of the block's 16 rows per column mu into HdT.  Rows of
+// Hd beyond the block's 16 and rows mu >= n of HdT are never written (zero from set-up).
 __global__ void __launch_bounds__(256)
 k_slice_ht(const double* __restrict__ Ht, long R, int n, Planes Hd, Planes HdT,
            int* __restrict__ ex) {
-  __shared__ __align__(16) __nv_bfloat16 tile[NDIG][64][40];   // [s][column k][row r] (+8 pad)
-  __shared__ int es[32];
+  __shared__ __align__(16) __nv_bfloat16 tile[NDIG][128][24];   // [s][column k][row r] (+8 pad)
+  __shared__ int es[16];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long r0 = (long)blockIdx.x * 32;
-  for (int i = 0; i < 4; ++i) {
-    const int row = warp * 4 + i;
+  const long r0 = (long)blockIdx.x * 16;
+  for (int i = 0; i < 2; ++i) {
+    const int row = warp * 2 + i;
     const long r = r0 + row;
     unsigned long long mx = 0;
     if (r < R)
@@ -593,17 +595,30 @@ k_slice_ht(const double* __restrict__ Ht, long R, int n, Planes Hd, Planes HdT,
   }
   __syncthreads();
   const long kend = Hd.nkb * BK;            // a multiple of 16
-  const long r = r0 + lane;                 // phase A: this thread's row
+  const int rr = threadIdx.x & 15, kc = threadIdx.x >> 4;   // digit pass: row, 8-column group
+  const long r = r0 + rr;
   const bool live = r < R;
-  const int e = es[lane];
+  const int e = es[rr];
   const double* hrow = Ht + r * n;
-  const int kk = threadIdx.x >> 2, r8 = (threadIdx.x & 3) * 8;   // phase B: column, 8 rows
-  for (long k0 = 0; k0 < kend; k0 += 64) {
-    const long k = k0 + warp * 8;
+  for (long k0 = 0; k0 < kend; k0 += 128) {
+    const long k = k0 + kc * 8;
     if (k < kend) {
+      double x[8];
+      if (live && (n & 1) == 0 && k + 8 <= n) {
+        // 16-byte loads (rows start 16-byte aligned when n is even)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const double2 t = *(const double2*)(hrow + k + 2 * j);
+          x[2 * j] = t.x;
+          x[2 * j + 1] = t.y;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = (live && k + j < n) ? hrow[k + j] : 0.0;
+      }
       __nv_bfloat16 d[8][NDIG];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) digits_of((live && k + j < n) ? hrow[k + j] : 0.0, e, d[j]);
+      for (int j = 0; j < 8; ++j) digits_of(x[j], e, d[j]);
 #pragma unroll
       for (int s = 0; s < NDIG; ++s) {
         uint4 v;
@@ -611,17 +626,24 @@ k_slice_ht(const double* __restrict__ Ht, long R, int n, Planes Hd, Planes HdT,
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           pv[j] = d[j][s];
-          tile[s][warp * 8 + j][lane] = d[j][s];
+          tile[s][kc * 8 + j][rr] = d[j][s];
         }
         if (r < Hd.Rpad) *(uint4*)(Hd.p + Hd.idx(s, r, k)) = v;
       }
     }
     __syncthreads();
-    const long mu = k0 + kk;
-    if (mu < n && r0 + r8 < HdT.nkb * BK) {
-#pragma unroll
-      for (int s = 0; s < NDIG; ++s)
-        *(uint4*)(HdT.p + HdT.idx(s, mu, r0 + r8)) = *(const uint4*)&tile[s][kk][r8];
+    // transposed: (plane s, column mu) pairs, 16 rows = 32 bytes each
+    if (r0 + 16 <= HdT.nkb * BK) {
+      for (int q = threadIdx.x; q < NDIG * 128; q += 256) {
+        const int s = q >> 7, kk = q & 127;
+        const long mu = k0 + kk;
+        if (mu < n) {
+          uint4* dst = (uint4*)(HdT.p + HdT.idx(s, mu, r0));
+          const uint4* src = (const uint4*)&tile[s][kk][0];
+          dst[0] = src[0];
+          dst[1] = src[1];
+        }
+      }
     }
     __syncthreads();
   }
@@ -1010,7 +1032,7 @@ las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaSt
   // chunk views: same allocations, the chunk's own K extent for the transposed planes
   Planes HdT = s->HdigT;
   HdT.K = R;
-  k_slice_ht<<<(unsigned)((R + 31) / 32), 256, 0, st>>>(Ht, R, s->n, s->Hdig, HdT, s->Hexp);
+  k_slice_ht<<<(unsigned)((R + 15) / 16), 256, 0, st>>>(Ht, R, s->n, s->Hdig, HdT, s->Hexp);
   las_count_launch();
   {
     cudaError_t e = cudaGetLastError();
