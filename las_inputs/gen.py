@@ -106,6 +106,17 @@ def packed_B(seed: int, n: int, naux: int, out: np.ndarray | None = None,
     return out
 
 
+def packed_B_rows(seed: int, n: int, naux: int, l0: int, l1: int) -> np.ndarray:
+    """Rows [l0, l1) of the full-size packed B of `packed_B(seed, n, naux)` (same counters and
+    decay), for checks on a slice of a workload too large to evaluate on the host."""
+    P = npair(n)
+    decay = _tril_decay(n)
+    out = np.empty((l1 - l0, P), dtype=np.float64)
+    for L in range(l0, l1):
+        out[L - l0] = normals(seed, 0, L * P, P) * decay * np.exp(-L / naux)
+    return out
+
+
 def one_electron_h(seed: int, n: int) -> np.ndarray:
     z = normals(seed, 1, 0, npair(n)) * _tril_decay(n)
     h = np.zeros((n, n))
