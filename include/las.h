@@ -225,6 +225,12 @@ las_status las_split_gemm(long M, long N, long K, const double* A, long lda, con
 las_status las_split_gemm_noalloc(long M, long N, long K, const double* A, long lda,
                                   const double* B, long ldb, double* C, long ldc, void* stream);
 
+/* Self-test of the device-side failure detection (no counterpart in the paper): one kernel waits
+ * on a barrier that is never signalled, with a short poll limit.  Returns LAS_ERR_TIMEOUT when
+ * the bounded wait gave up and the kernel returned as designed (the device stays usable),
+ * LAS_ERR_CUDA on a CUDA error.  stream: cudaStream_t or NULL. */
+las_status las_selftest_bounded_wait(void* stream);
+
 /* Number of kernels this library has launched in this process so far (all contexts). */
 long las_kernel_launches(void);
 

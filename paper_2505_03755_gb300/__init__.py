@@ -4,8 +4,8 @@ The compute lives in liblasdf.so (C ABI declared in include/las.h); this package
 Python binding.  There is no CPU fallback.
 """
 from .las import (EXPORTS, LAS_FP64, LAS_SPLIT_BF16, LasDF, LasError, energy_grad_batched,
-                  kernel_launches, las_energy, load_library, split_gemm)
+                  kernel_launches, las_energy, load_library, selftest_bounded_wait, split_gemm)
 
 __all__ = ["EXPORTS", "LAS_FP64", "LAS_SPLIT_BF16", "LasDF", "LasError", "las_energy",
            "load_library", "kernel_launches",
-           "split_gemm", "energy_grad_batched"]
+           "split_gemm", "energy_grad_batched", "selftest_bounded_wait"]

@@ -1347,6 +1347,51 @@ las_status frag_split_chunk(SplitState* s, FragSplit* f, int l0, int nL, double*
 }
 
 // ------------------------------------------------------------------------------------------
+// Self-test of the bounded waits: one CTA waits on an mbarrier that nothing ever arrives on,
+// with a short poll limit; the wait must give up, record LAS_ERR_TIMEOUT and let the kernel
+// return, leaving the context usable.
+// ------------------------------------------------------------------------------------------
+namespace lasdf_split {
+__global__ void k_selftest_wait(int* status, long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    sm100::mbar_init(&bar, 1);
+    abort_flag = 0;
+    sm100::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    sm100::mbar_wait(&bar, 0, (volatile int*)&abort_flag, status, LAS_ERR_TIMEOUT, 0, limit);
+  __syncthreads();
+}
+}  // namespace lasdf_split
+
+extern "C" las_status las_selftest_bounded_wait(void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int* status = nullptr;
+  LAS_CUDA_TRY(cudaMalloc(&status, sizeof(int)));
+  las_status rc = LAS_OK;
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    k_selftest_wait<<<1, 32, 0, st>>>(status, 1L << 16);
+    las_count_launch();
+    e = cudaGetLastError();
+  }
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "bounded-wait self-test", __FILE__, __LINE__);
+    rc = LAS_ERR_CUDA;
+  } else {
+    rc = (las_status)h;
+  }
+  cudaFree(status);
+  return rc;
+}
+
+// ------------------------------------------------------------------------------------------
 // Allocation-free variant of las_split_gemm
 //
 // Some callers cannot allocate device memory at the point where they need a product: code that

@@ -65,13 +65,14 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
 // another role already aborted.  sleep_ns > 0 backs off between polls (for waiters whose latency
 // does not matter, so that they leave issue slots to the latency-critical warps).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
-                                          int* status, int code, unsigned sleep_ns = 0) {
+                                          int* status, int code, unsigned sleep_ns = 0,
+                                          long limit = 1L << 24) {
   for (long it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (sleep_ns) __nanosleep(sleep_ns);
     if ((it & 1023) == 1023) {
       if (*abort) return false;
-      if (it > (1L << 24)) {  // ~seconds: far beyond any legitimate wait
+      if (it > limit) {  // the default, 2^24 polls, is seconds: far beyond any legitimate wait
         *abort = 1;
         atomicCAS(status, 0, code);
         return false;

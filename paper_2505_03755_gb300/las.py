@@ -22,7 +22,8 @@ EXPORTS = ["las_create", "las_destroy", "las_set_stream", "las_sync", "las_devic
            "las_df_transform", "las_df_jk", "las_energy", "las_energy_grad",
            "las_energy_grad_host", "las_set_timing", "las_stage_times", "las_kernel_launches",
            "las_split_gemm_workspace", "las_split_gemm", "las_energy_grad_batched",
-           "las_autotune", "las_df_jk_density", "las_status_str"]
+           "las_autotune", "las_df_jk_density", "las_frag_ao2mo", "las_veff",
+           "las_split_gemm_noalloc", "las_selftest_bounded_wait", "las_status_str"]
 
 
 class LasError(RuntimeError):
@@ -83,6 +84,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.las_frag_ao2mo.restype = i
     lib.las_veff.argtypes = [vp, vp, vp, i, vp, vp, i, vp, vp]
     lib.las_veff.restype = i
+    lib.las_selftest_bounded_wait.argtypes = [vp]
+    lib.las_selftest_bounded_wait.restype = i
     lib.las_kernel_launches.argtypes = []
     lib.las_kernel_launches.restype = ctypes.c_long
     lib.las_status_str.argtypes = [i]
@@ -270,6 +273,15 @@ class LasDF:
         _check(self._lib.las_df_transform(self._h, _ptr(C), p0, p1, _ptr(lmu), _ptr(lpu)),
                "las_df_transform")
         return lmu, lpu
+
+
+def selftest_bounded_wait(stream=None) -> int:
+    """Run the device-side bounded-wait self-test; returns the las_status code it reports
+    (LAS_ERR_TIMEOUT = 4 when the wait gave up as designed)."""
+    import torch
+    lib = load_library()
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    return int(lib.las_selftest_bounded_wait(st))
 
 
 def energy_grad_batched(problems, items, stream=None):
