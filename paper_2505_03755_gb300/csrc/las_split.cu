@@ -744,16 +744,20 @@ static las_status make_plane_map(CUtensorMap* m, const Planes& P, int box_rows) 
   return r == CUDA_SUCCESS ? LAS_OK : LAS_ERR_INTERNAL;
 }
 
+// The launch attribute is a per-device setting: set once for each device that uses the kernel
+// (a repeated set from two threads is harmless).
 static las_status ozaki_prepare() {
-  static int done = 0;
-  if (done) return LAS_OK;
+  static volatile int done[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LAS_ERR_CUDA;
+  if (done[dev]) return LAS_OK;
   cudaError_t e = cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        SMEM_BYTES);
   if (e != cudaSuccess) {
     las_record_cuda_error(e, "cudaFuncSetAttribute(k_ozaki)", __FILE__, __LINE__);
     return LAS_ERR_CUDA;
   }
-  done = 1;
+  done[dev] = 1;
   return LAS_OK;
 }
 
