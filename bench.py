@@ -286,7 +286,7 @@ NDIG_PRODUCTS = 21     # digit products of the split-precision GEMM (6 digits, s
 # ncu capture of the same launch on the first 200 auxiliary functions (200 x 1200 rows;
 # profiles/k_ozaki_half_transform_nao1200_naux200.md), scaled to a full launch by the rows it
 # processes (the traffic is proportional to the rows: digits of B read once, H written once).
-S1_TRAFFIC_PER_ROW = (3.535900e9 + 0.386882e9) / (200 * 1200)
+S1_TRAFFIC_PER_ROW = (3.534248e9 + 0.386613e9) / (200 * 1200)
 
 
 def roofline_for(prec, r, work, peaks, s):
