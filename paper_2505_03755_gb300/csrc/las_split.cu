@@ -1223,12 +1223,12 @@ las_status frag_split_create(FragSplit** out, int n, int nmo, int ma, int Lc, cu
   f->ma = ma;
   f->Lc = Lc;
   const long n2 = (long)nmo * nmo, R1 = (long)Lc * nmo;
-  const size_t parts[] = {planes_bytes(nmo, n),          rup((size_t)nmo * 4, 256),
-                          planes_bytes(R1, n),           rup((size_t)R1 * 4, 256),
-                          planes_bytes(n2, Lc),          rup((size_t)n2 * 4, 256),
-                          planes_bytes((long)ma * ma, Lc), rup((size_t)ma * ma * 4, 256),
-                          planes_bytes((long)nmo * ma, Lc), rup((size_t)nmo * ma * 4, 256),
-                          (size_t)n2 * 8};
+  const size_t parts[] = {planes_bytes(nmo, n),             (size_t)nmo * 4,
+                          planes_bytes(R1, n),              (size_t)R1 * 4,
+                          planes_bytes(n2, Lc),             (size_t)n2 * 4,
+                          planes_bytes((long)ma * ma, Lc),  (size_t)ma * ma * 4,
+                          planes_bytes((long)nmo * ma, Lc), (size_t)nmo * ma * 4,
+                          (size_t)n2 * 8};   // each part is rounded up to 256 bytes below
   size_t total = 0;
   for (size_t b : parts) total += rup(b, 256);
   if (cudaMalloc(&f->blob, total) != cudaSuccess) {
