@@ -105,7 +105,8 @@ las_status las_df_jk(las_ctx* ctx, const double* C, double* J, double* K);
  * the columns of its sign; zero weights are skipped).  The call reads the two column counts back
  * to the host once (one synchronisation of the context's stream), so it is not graph-capturable.
  * Requires r <= ncore + sum(nact) of the context (create a JK context with ncore >= r and no
- * fragments for densities of other ranks).  J, K: device [nao][nao]; either may be NULL. */
+ * fragments for densities of other ranks).  r = 0 (Cx, w may then be NULL) gives J = K = 0.
+ * J, K: device [nao][nao]; either may be NULL. */
 las_status las_df_jk_density(las_ctx* ctx, const double* Cx, const double* w, int r, double* J,
                              double* K);
 

@@ -564,7 +564,7 @@ extern "C" las_status las_df_jk(las_ctx* x, const double* C, double* J, double* 
 
 extern "C" las_status las_df_jk_density(las_ctx* x, const double* Cx, const double* w, int r,
                                         double* J, double* K) {
-  if (!x || !Cx || !w || r < 0) return LAS_ERR_ARG;
+  if (!x || r < 0 || (r > 0 && (!Cx || !w))) return LAS_ERR_ARG;   // r = 0: D = 0
   if (r > x->o) return LAS_ERR_ARG;
   if (!J && !K) return LAS_OK;
   const int n = x->n;

@@ -79,3 +79,20 @@ def test_frag_ao2mo_rejects_bad_ranges():
         with pytest.raises(RuntimeError):
             las.frag_ao2mo(dev(M), a0, ma)
     las.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("split", 1e-10)])
+@pytest.mark.parametrize("a0,ma", [(0, 24), (17, 7)])
+def test_frag_ao2mo_active_range_edges(precision, tol, a0, ma):
+    """Every orbital active (ma = nmo), and the active block ending at the last orbital."""
+    torch_cuda()
+    built()
+    from paper_2505_03755_gb300 import LasDF
+    s, M = _case(24, 70, 906)
+    ppaa_r, papa_r = O.frag_ao2mo(s.Bp, s.nao, M, a0, ma)
+    las = LasDF(dev(s.Bp), s.nao, s.naux, s.nmo, s.ncore, s.nact, precision=precision)
+    ppaa, papa = las.frag_ao2mo(dev(M), a0, ma)
+    las.sync()
+    assert np.abs(ppaa.cpu().numpy() - ppaa_r).max() <= tol * np.abs(ppaa_r).max()
+    assert np.abs(papa.cpu().numpy() - papa_r).max() <= tol * np.abs(papa_r).max()
+    las.close()

@@ -57,3 +57,27 @@ def test_df_jk_density_spin_densities_of_a_las_state():
         assert np.abs(J.cpu().numpy() - Jr).max() <= 1e-11 * np.abs(Jr).max()
         assert np.abs(K.cpu().numpy() - Kr).max() <= 1e-11 * np.abs(Kr).max()
         las.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("split", 1e-11)])
+def test_df_jk_density_weight_edge_cases(precision, tol):
+    """All weights negative, zero weights mixed in, and the empty density (r = 0)."""
+    torch_cuda()
+    built()
+    from paper_2505_03755_gb300 import LasDF
+    s = make_system(41, 60, 20, [], seed=6060)
+    rng = np.random.default_rng(3)
+    las = LasDF(dev(s.Bp), s.nao, s.naux, s.nmo, s.ncore, [], precision=precision)
+    Cx = rng.standard_normal((s.nao, 9))
+    for w in (-np.abs(rng.standard_normal(9)),
+              np.where(np.arange(9) % 3 == 0, 0.0, rng.standard_normal(9))):
+        D = Cx @ np.diag(w) @ Cx.T
+        (Jr,), (Kr,) = O.df_jk(s.Bp, s.nao, [D])
+        J, K = las.df_jk_density(dev(Cx), dev(w))
+        las.sync()
+        assert np.abs(J.cpu().numpy() - Jr).max() <= tol * np.abs(Jr).max()
+        assert np.abs(K.cpu().numpy() - Kr).max() <= tol * np.abs(Kr).max()
+    J, K = las.df_jk_density(dev(np.zeros((s.nao, 0))), dev(np.zeros(0)))
+    las.sync()
+    assert not J.abs().max().item() and not K.abs().max().item()
+    las.close()

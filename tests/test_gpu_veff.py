@@ -67,3 +67,23 @@ def test_veff_self_potential_embedded_basis(precision, tol):
     assert np.abs(va.cpu().numpy() - va_r).max() <= tol * scale
     assert np.abs(vb.cpu().numpy() - vb_r).max() <= tol * scale
     las.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("split", 1e-11)])
+def test_veff_one_spin_empty(precision, tol):
+    """gamma_beta = 0 (rank 0): v_alpha = J[gamma_a] - K[gamma_a], v_beta = J[gamma_a]."""
+    torch_cuda()
+    built()
+    from paper_2505_03755_gb300 import LasDF
+    s = make_system(33, 50, 6, [], seed=4444)
+    C_c = np.ascontiguousarray(s.C[:, :s.ncore])
+    ga = C_c @ C_c.T
+    va_r, vb_r = O.embedding_potentials(s.Bp, s.nao, ga, np.zeros_like(ga))
+    las = LasDF(dev(s.Bp), s.nao, s.naux, s.nmo, s.ncore, [], precision=precision)
+    va, vb = las.veff(dev(C_c), dev(np.ones(s.ncore)), dev(np.zeros((s.nao, 0))),
+                      dev(np.zeros(0)))
+    las.sync()
+    scale = max(np.abs(va_r).max(), np.abs(vb_r).max())
+    assert np.abs(va.cpu().numpy() - va_r).max() <= tol * scale
+    assert np.abs(vb.cpu().numpy() - vb_r).max() <= tol * scale
+    las.close()
