@@ -240,6 +240,64 @@ def energy_grad(Bp: np.ndarray, n: int, h: np.ndarray, C: np.ndarray, ncore: int
     return out
 
 
+def grad_derivative(Bp: np.ndarray, n: int, h: np.ndarray, C: np.ndarray, ncore: int,
+                    dm1s: list[np.ndarray], dm2: list[np.ndarray], dC: np.ndarray) -> dict:
+    """Directional derivative of dE/dC along dC at fixed fragment RDMs: the linearisation of
+    the gradient formulas of `energy_grad` term by term,
+        dDc = 2 (dC_c C_c^T + C_c dC_c^T),   dDa = dC_a D C_a^T + C_a D dC_a^T,
+        dF^I = J[dDc] - K[dDc]/2,            dF^A = J[dDa] - K[dDa]/2,
+        dG[:, core] = 4 (dF^I + dF^A) C_c + 4 (F^I + F^A) dC_c,
+        dG[:, act]  = 2 dF^I C_a D + 2 F^I dC_a D + 2 sum_vwx d(mu v|wx) Gamma_uvwx,
+        d(mu v|wx)  = sum_P (b^P dC_a)_{mu v} (C_a^T b^P C_a)_wx
+                      + (b^P C_a)_{mu v} (dC_a^T b^P C_a + C_a^T b^P dC_a)_wx.
+    Returns G, dG (n x nmo) and the matching quantities of the orbital-rotation gradient."""
+    nact = [d.shape[-1] for d in dm1s]
+    a = int(sum(nact))
+    C_c, C_a = C[:, :ncore], C[:, ncore:ncore + a]
+    dC_c, dC_a = dC[:, :ncore], dC[:, ncore:ncore + a]
+    Dact, Gact = active_rdms(dm1s, dm2) if a else (np.zeros((0, 0)), np.zeros((0,) * 4))
+    Dc = 2.0 * C_c @ C_c.T
+    Da = C_a @ Dact @ C_a.T
+    dDc = 2.0 * (dC_c @ C_c.T + C_c @ dC_c.T)
+    dDa = dC_a @ Dact @ C_a.T + C_a @ Dact @ dC_a.T
+    (Jc, Ja, dJc, dJa), (Kc, Ka, dKc, dKa) = df_jk(Bp, n, [Dc, Da, dDc, dDa])
+    FI, FA = h + Jc - 0.5 * Kc, Ja - 0.5 * Ka
+    dFI, dFA = dJc - 0.5 * dKc, dJa - 0.5 * dKa
+    G = np.zeros_like(C)
+    dG = np.zeros_like(C)
+    G[:, :ncore] = 4.0 * (FI + FA) @ C_c
+    dG[:, :ncore] = 4.0 * (dFI + dFA) @ C_c + 4.0 * (FI + FA) @ dC_c
+    if a:
+        mveri = np.zeros((n, a, a, a))
+        dmveri = np.zeros((n, a, a, a))
+        for _, _, b in p_blocks(Bp, n):
+            bmv = b @ C_a                                            # (b^P C_a)_{mu v}
+            dbmv = b @ dC_a
+            buv = np.einsum("mu,Pmv->Puv", C_a, bmv, optimize=True)  # C_a^T b^P C_a
+            dbuv = np.einsum("mu,Pmv->Puv", dC_a, bmv, optimize=True)
+            dbuv = dbuv + dbuv.transpose(0, 2, 1)                    # b^P symmetric
+            mveri += np.einsum("Pmv,Pwx->mvwx", bmv, buv, optimize=True)
+            dmveri += (np.einsum("Pmv,Pwx->mvwx", dbmv, buv, optimize=True)
+                       + np.einsum("Pmv,Pwx->mvwx", bmv, dbuv, optimize=True))
+        G[:, ncore:ncore + a] = 2.0 * FI @ C_a @ Dact + 2.0 * np.einsum(
+            "mvwx,uvwx->mu", mveri, Gact, optimize=True)
+        dG[:, ncore:ncore + a] = (2.0 * dFI @ C_a @ Dact + 2.0 * FI @ dC_a @ Dact
+                                  + 2.0 * np.einsum("mvwx,uvwx->mu", dmveri, Gact,
+                                                    optimize=True))
+    return dict(G=G, dG=dG)
+
+
+def orbital_hvp(Bp: np.ndarray, n: int, h: np.ndarray, C: np.ndarray, ncore: int,
+                dm1s: list[np.ndarray], dm2: list[np.ndarray], X: np.ndarray) -> dict:
+    """Derivative of the orbital-rotation gradient g(C) = C^T G - (C^T G)^T along the rotation
+    C(t) = C exp(t X) at t = 0 (X antisymmetric, nmo x nmo), at fixed fragment RDMs:
+        Dg = (C X)^T G + C^T dG - transpose,   dG = dE/dC differentiated along dC = C X."""
+    dC = C @ X
+    r = grad_derivative(Bp, n, h, C, ncore, dm1s, dm2, dC)
+    M = dC.T @ r["G"] + C.T @ r["dG"]
+    return dict(G=r["G"], dG=r["dG"], dC=dC, Dg=M - M.T)
+
+
 def system_energy_grad(sysm, with_grad: bool = True, l0: int = 0, l1: int | None = None) -> dict:
     return energy_grad(sysm.Bp, sysm.nao, sysm.h, sysm.C, sysm.ncore, sysm.dm1s, sysm.dm2,
                        with_grad=with_grad, l0=l0, l1=l1)

@@ -214,6 +214,60 @@ def test_embedding_potentials_match_fock_terms(small3):
     assert np.abs(0.5 * (va + vb) - ref).max() < 1e-11 * np.abs(ref).max()
 
 
+def _directions(s, seed, k=2):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(k):
+        X = rng.standard_normal((s.nmo, s.nmo))
+        out.append((X - X.T) / np.sqrt(2.0))
+    return out
+
+
+def _egrad(s, C):
+    return O.energy_grad(s.Bp, s.nao, s.h, C, s.ncore, s.dm1s, s.dm2)
+
+
+def test_grad_derivative_symmetric_and_exact_on_the_energy(small3):
+    """<dC2, dG(dC1)> = <dC1, dG(dC2)> (the Hessian of E(C) is symmetric), and along a line
+    E(C + t dC) is a quartic, so the five-point stencils give E'(0) and E''(0) exactly:
+    E'(0) = <G, dC>, E''(0) = <dC, dG(dC)>."""
+    s = small3
+    rng = np.random.default_rng(11)
+    dC1, dC2 = rng.standard_normal(s.C.shape), rng.standard_normal(s.C.shape)
+    r1 = O.grad_derivative(s.Bp, s.nao, s.h, s.C, s.ncore, s.dm1s, s.dm2, dC1)
+    r2 = O.grad_derivative(s.Bp, s.nao, s.h, s.C, s.ncore, s.dm1s, s.dm2, dC2)
+    a12, a21 = np.sum(dC2 * r1["dG"]), np.sum(dC1 * r2["dG"])
+    assert abs(a12 - a21) <= 1e-10 * max(abs(a12), 1.0)
+    tau = 0.05
+    E = {t: _egrad(s, s.C + t * tau * dC1)["E"] for t in (-2, -1, 0, 1, 2)}
+    d1 = (E[-2] - 8 * E[-1] + 8 * E[1] - E[2]) / (12 * tau)
+    d2 = (-E[-2] + 16 * E[-1] - 30 * E[0] + 16 * E[1] - E[2]) / (12 * tau * tau)
+    assert abs(d1 - np.sum(r1["G"] * dC1)) <= 1e-8 * abs(d1)
+    assert abs(d2 - np.sum(dC1 * r1["dG"])) <= 1e-7 * abs(d2)
+
+
+def test_grad_derivative_finite_differences(cfg0):
+    s = cfg0
+    dC = np.random.default_rng(12).standard_normal(s.C.shape)
+    r = O.grad_derivative(s.Bp, s.nao, s.h, s.C, s.ncore, s.dm1s, s.dm2, dC)
+    eps = 1e-4
+    fd = (_egrad(s, s.C + eps * dC)["G"] - _egrad(s, s.C - eps * dC)["G"]) / (2 * eps)
+    assert np.abs(fd - r["dG"]).max() <= 1e-6 * np.abs(r["dG"]).max()
+
+
+def test_orbital_hvp_finite_differences(small3):
+    """Dg against central differences of g(C exp(t X))."""
+    s = small3
+    for X in _directions(s, 13):
+        r = O.orbital_hvp(s.Bp, s.nao, s.h, s.C, s.ncore, s.dm1s, s.dm2, X)
+        eps = 1e-5
+        gp = _egrad(s, s.C @ sl.expm(eps * X))["gorb"]
+        gm = _egrad(s, s.C @ sl.expm(-eps * X))["gorb"]
+        fd = (gp - gm) / (2 * eps)
+        assert np.abs(fd - r["Dg"]).max() <= 1e-6 * np.abs(r["Dg"]).max()
+        assert np.abs(r["Dg"] + r["Dg"].T).max() <= 1e-12 * np.abs(r["Dg"]).max()
+
+
 @pytest.mark.parametrize("which", ["cfg0", "small3"])
 def test_energy_three_ways(which, request):
     s = request.getfixturevalue(which)
