@@ -134,6 +134,18 @@ las_status las_veff(las_ctx* ctx, const double* C_alpha, const double* w_alpha, 
                     const double* C_beta, const double* w_beta, int r_beta, double* v_alpha,
                     double* v_beta);
 
+/* Orbital Hessian-vector product at fixed fragment RDMs (the orbital part of the second-order
+ * step of Eq. flas; the paper leaves the forms to its references): for an antisymmetric
+ * X (device [nmo][nmo]) and dC = C X,
+ *   dG = directional derivative of dE/dC along dC                      (device [nao][nmo])
+ *   Dg = d/dt g(C exp(tX)) at t = 0 = (C X)^T G + C^T dG - transpose   (device [nmo][nmo],
+ *        NULL to skip; g = C^T dE/dC - transpose is the orbital-rotation gradient)
+ * dE/dC is cubic in C, so dG is formed exactly (up to rounding) by a five-point stencil over four
+ * gradient evaluations along C + t dC (one more for Dg).  The step is set from max|C| and
+ * max|dC|, read back once (one stream synchronisation: not graph-capturable). */
+las_status las_orbital_hvp(las_ctx* ctx, const double* C, const double* h, const double* dm1s,
+                           const double* dm2, const double* X, double* dG, double* Dg);
+
 /* LAS energy.  h: device [nao][nao] one-electron Hamiltonian (symmetric).
  * dm1s: device, per fragment K the spin-separated 1-RDM [2][m_K][m_K] (alpha, beta),
  *       concatenated over fragments.

@@ -78,6 +78,8 @@ struct las_ctx {
   int fnmo, fma;
   FragSplit* fsplit;
   double *vJ, *vK;   // scratch of las_veff (allocated by its first call)
+  double *hdC, *hCt, *hGt, *hG;   // scratch of las_orbital_hvp (dC, C + t dC, G(C + t dC), G(C))
+  unsigned long long* hmax;       // [2] |C| and |dC| maxima (bit patterns)
   int* widx;          // [2*o + 2] columns of each weight sign and their counts (JK density)
   int wcount[2];      // host copy of those counts
   // timing: a ring of LAS_TIMING_RING evaluations x 6 stage marks, read without per-call syncs
@@ -121,7 +123,8 @@ static void free_all(las_ctx* x) {
     if (p) cudaFree(p);
   if (x->split) split_destroy(x->split);
   if (x->fsplit) frag_split_destroy(x->fsplit);
-  for (double* q : {x->fH, x->fT, x->fpart, x->vJ, x->vK})
+  if (x->hmax) cudaFree(x->hmax);
+  for (double* q : {x->fH, x->fT, x->fpart, x->vJ, x->vK, x->hdC, x->hCt, x->hGt, x->hG})
     if (q) cudaFree(q);
   if (x->ev) {
     for (int i = 0; i < LAS_TIMING_RING * LAS_MARKS; ++i)
@@ -653,6 +656,75 @@ extern "C" las_status las_veff(las_ctx* x, const double* Ca, const double* wa, i
   launch_scale(vb, nn, -1.0, x->stream);
   launch_axpy(vb, va, 1.0, nn, x->stream);         // vb = J[D] - K_b
   launch_axpy(va, x->vK, -1.0, nn, x->stream);     // va = J[D] - K_a
+  return check_launch();
+}
+
+// ------------------------------------------------------------------------------------------
+// Orbital Hessian-vector product at fixed fragment RDMs
+// ------------------------------------------------------------------------------------------
+// dE/dC is a cubic polynomial in C (H = b C and the per-L matrices T = C^T b C, W(T) are of
+// degree 1, 2, 2; G = [one-electron terms, linear in C] + sum_L H_L W_L), so along the line
+// C + t dC the five-point stencil
+//     dG = [G(-2 tau) - 8 G(-tau) + 8 G(tau) - G(2 tau)] / (12 tau),   G(t) = G(C + t dC),
+// which is exact for polynomials up to degree four, is the directional derivative without any
+// truncation error: only the rounding of the four evaluations enters, amplified by about
+// (1 + 2 r)^3 / r with r = tau max|dC| / max|C| (tau is chosen for r = 1/4).
+extern "C" las_status las_orbital_hvp(las_ctx* x, const double* C, const double* h,
+                                      const double* dm1s, const double* dm2, const double* X,
+                                      double* dG, double* Dg) {
+  if (!x || !C || !h || !X || !dG) return LAS_ERR_ARG;
+  if (x->a > 0 && (!dm1s || !dm2)) return LAS_ERR_ARG;
+  const int n = x->n, nmo = x->nmo;
+  const long nC = (long)n * nmo;
+  las_status st = LAS_OK;
+  if (!x->hdC) {
+    for (double** q : {&x->hdC, &x->hCt, &x->hGt, &x->hG})
+      if ((st = dalloc(x, (void**)q, sizeof(double) * nC)) != LAS_OK) return st;
+    if ((st = dalloc(x, (void**)&x->hmax, 2 * sizeof(unsigned long long))) != LAS_OK) return st;
+  }
+  // dC = C X
+  {
+    StridedA Ac{C, 0, nmo, 1};
+    StridedA Bx{X, 0, nmo, 1};
+    StridedC Cd{x->hdC, 0, nmo, 1, 1.0, 0};
+    gemm_f64(n, nmo, nmo, 1, 1, Ac, Bx, Cd, x->stream);
+  }
+  // step: tau max|dC| = max|C| / 4 (the maxima are read back once)
+  LAS_CUDA_TRY(cudaMemsetAsync(x->hmax, 0, 2 * sizeof(unsigned long long), x->stream));
+  launch_absmax_bits(C, nC, x->hmax, x->stream);
+  launch_absmax_bits(x->hdC, nC, x->hmax + 1, x->stream);
+  unsigned long long mx[2] = {0, 0};
+  LAS_CUDA_TRY(cudaMemcpyAsync(mx, x->hmax, sizeof(mx), cudaMemcpyDeviceToHost, x->stream));
+  LAS_CUDA_TRY(cudaStreamSynchronize(x->stream));
+  double cmax, dmax;
+  memcpy(&cmax, &mx[0], 8);
+  memcpy(&dmax, &mx[1], 8);
+  LAS_CUDA_TRY(cudaMemsetAsync(dG, 0, (size_t)nC * 8, x->stream));
+  if (dmax > 0.0) {
+    const double tau = 0.25 * cmax / dmax;
+    const double w[4] = {1.0, -8.0, 8.0, -1.0};
+    const double t[4] = {-2.0, -1.0, 1.0, 2.0};
+    for (int k = 0; k < 4; ++k) {
+      LAS_CUDA_TRY(cudaMemcpyAsync(x->hCt, C, (size_t)nC * 8, cudaMemcpyDeviceToDevice,
+                                   x->stream));
+      launch_axpy(x->hCt, x->hdC, t[k] * tau, nC, x->stream);
+      if ((st = evaluate(x, x->hCt, h, dm1s, dm2, x->dE, x->hGt, nullptr)) != LAS_OK) return st;
+      launch_axpy(dG, x->hGt, w[k] / (12.0 * tau), nC, x->stream);
+    }
+  }
+  if (Dg) {
+    // Dg = (C X)^T G + C^T dG - transpose  (virtual columns of G and dG are zero)
+    if ((st = evaluate(x, C, h, dm1s, dm2, x->dE, x->hG, nullptr)) != LAS_OK) return st;
+    StridedA Ad{x->hdC, 0, 1, nmo};
+    StridedA Bg{x->hG, 0, nmo, 1};
+    StridedC Cm{x->M, 0, x->op, 1, 1.0, 0};
+    gemm_f64(nmo, x->o, n, 1, 1, Ad, Bg, Cm, x->stream);
+    StridedA Acc{C, 0, 1, nmo};
+    StridedA Bdg{dG, 0, nmo, 1};
+    StridedC Cm2{x->M, 0, x->op, 1, 1.0, 1};
+    gemm_f64(nmo, x->o, n, 1, 1, Acc, Bdg, Cm2, x->stream);
+    launch_antisym(x->M, nmo, x->o, x->op, Dg, x->stream);
+  }
   return check_launch();
 }
 

@@ -395,6 +395,25 @@ k_trace_ht(const double* __restrict__ Ht, const double* __restrict__ CT, int r, 
   if (threadIdx.x == 0) vc[b] = 2.0 * t;
 }
 
+// out (atomic max) = max |a[i]| as an ordered bit pattern (block tree, then one atomic per block)
+__global__ void __launch_bounds__(256)
+k_absmax_bits(const double* __restrict__ a, long count, unsigned long long* out) {
+  __shared__ unsigned long long red[256];
+  unsigned long long m = 0;
+  for (long i = blockIdx.x * 256L + threadIdx.x; i < count; i += (long)gridDim.x * 256) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a[i]) & 0x7FFFFFFFFFFFFFFFull;
+    m = b > m ? b : m;
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w && red[threadIdx.x + w] > red[threadIdx.x])
+      red[threadIdx.x] = red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && red[0]) atomicMax(out, red[0]);
+}
+
 }  // namespace lasdf
 
 using namespace lasdf;
@@ -500,6 +519,12 @@ void launch_assemble_grad(const double* Out, const double* hC, const double* dm1
 void launch_energy_final(const double* eps, int X, const double* hmo, int op,
                          const double* dm1s, const FragInfo& fi, double* E, cudaStream_t s) {
   k_energy_final<<<1, 256, 0, s>>>(eps, X, hmo, op, dm1s, fi, E);
+  las_count_launch();
+}
+
+void launch_absmax_bits(const double* a, long count, unsigned long long* out, cudaStream_t s) {
+  if (count <= 0) return;
+  k_absmax_bits<<<(unsigned)std::min<long>(nblk(count, 256), 1024), 256, 0, s>>>(a, count, out);
   las_count_launch();
 }
 

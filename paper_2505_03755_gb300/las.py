@@ -23,7 +23,8 @@ EXPORTS = ["las_create", "las_destroy", "las_set_stream", "las_sync", "las_devic
            "las_energy_grad_host", "las_set_timing", "las_stage_times", "las_kernel_launches",
            "las_split_gemm_workspace", "las_split_gemm", "las_energy_grad_batched",
            "las_autotune", "las_df_jk_density", "las_frag_ao2mo", "las_veff",
-           "las_split_gemm_noalloc", "las_selftest_bounded_wait", "las_status_str"]
+           "las_split_gemm_noalloc", "las_selftest_bounded_wait", "las_orbital_hvp",
+           "las_status_str"]
 
 
 class LasError(RuntimeError):
@@ -84,6 +85,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.las_frag_ao2mo.restype = i
     lib.las_veff.argtypes = [vp, vp, vp, i, vp, vp, i, vp, vp]
     lib.las_veff.restype = i
+    lib.las_orbital_hvp.argtypes = [vp] * 8
+    lib.las_orbital_hvp.restype = i
     lib.las_selftest_bounded_wait.argtypes = [vp]
     lib.las_selftest_bounded_wait.restype = i
     lib.las_kernel_launches.argtypes = []
@@ -235,6 +238,18 @@ class LasDF:
         _check(self._lib.las_df_jk_density(self._h, _ptr(Cx), _ptr(w), int(Cx.shape[1]),
                                            _ptr(J), _ptr(K)), "las_df_jk_density")
         return J, K
+
+    def orbital_hvp(self, C, h, dm1s, dm2, X, want_Dg: bool = True):
+        """(dG, Dg): the derivative of dE/dC along dC = C X and of the orbital-rotation gradient
+        along C exp(tX), at fixed fragment RDMs (X antisymmetric nmo x nmo)."""
+        import torch
+        dev = C.device
+        dG = torch.empty((self.nao, self.nmo), dtype=torch.float64, device=dev)
+        Dg = torch.empty((self.nmo, self.nmo), dtype=torch.float64, device=dev) if want_Dg \
+            else None
+        _check(self._lib.las_orbital_hvp(self._h, _ptr(C), _ptr(h), _ptr(dm1s), _ptr(dm2),
+                                         _ptr(X), _ptr(dG), _ptr(Dg)), "las_orbital_hvp")
+        return dG, Dg
 
     def veff(self, C_alpha, w_alpha, C_beta, w_beta):
         """Effective potentials v_sigma = J[gamma_a + gamma_b] - K[gamma_sigma] (Eqs. v_emb,
