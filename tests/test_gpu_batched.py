@@ -92,3 +92,24 @@ def test_batched_graph_sees_new_inputs_on_replay():
         assert np.abs(it[5].cpu().numpy() - ref["G"]).max() <= 1e-8
     for L in las:
         L.close()
+
+
+def test_batched_many_systems_share_branches():
+    """More systems than graph branches (several per branch, shared out by size): every
+    problem bit-identical to its single-problem call, the smallest against the oracle."""
+    torch = torch_cuda()
+    systems = _systems(13, lambda sp: sorted(sp, key=lambda x: x["nao"]))
+    las, items, batched = _run(systems)
+    batched(las, items)
+    torch.cuda.synchronize()
+    got = [(float(it[4]), it[5].cpu().numpy()) for it in items]
+    for L, it, (e0, g0) in zip(las, items, got):
+        E, G = L.energy_grad(*it[:4])
+        L.sync()
+        assert float(E) == e0
+        assert np.array_equal(G.cpu().numpy(), g0)
+    ref = O.system_energy_grad(systems[0])
+    assert abs(got[0][0] - ref["E"]) <= 1e-8
+    assert np.abs(got[0][1] - ref["G"]).max() <= 1e-8
+    for L in las:
+        L.close()
