@@ -664,11 +664,12 @@ extern "C" las_status las_veff(las_ctx* x, const double* Ca, const double* wa, i
 // ------------------------------------------------------------------------------------------
 // dE/dC is a cubic polynomial in C (H = b C and the per-L matrices T = C^T b C, W(T) are of
 // degree 1, 2, 2; G = [one-electron terms, linear in C] + sum_L H_L W_L), so along the line
-// C + t dC the five-point stencil
-//     dG = [G(-2 tau) - 8 G(-tau) + 8 G(tau) - G(2 tau)] / (12 tau),   G(t) = G(C + t dC),
-// which is exact for polynomials up to degree four, is the directional derivative without any
+// C + t dC the four-point rule
+//     dG = [6 G(tau) - 2 G(-tau) - G(2 tau) - 3 G(0)] / (6 tau),   G(t) = G(C + t dC),
+// which is exact for polynomials up to degree three, is the directional derivative without any
 // truncation error: only the rounding of the four evaluations enters, amplified by about
-// (1 + 2 r)^3 / r with r = tau max|dC| / max|C| (tau is chosen for r = 1/4).
+// 2 (1 + 2 r)^3 / r with r = tau max|dC| / max|C| (tau is chosen for r = 1/4).  G(0) also
+// serves Dg.
 extern "C" las_status las_orbital_hvp(las_ctx* x, const double* C, const double* h,
                                       const double* dm1s, const double* dm2, const double* X,
                                       double* dG, double* Dg) {
@@ -700,21 +701,22 @@ extern "C" las_status las_orbital_hvp(las_ctx* x, const double* C, const double*
   memcpy(&cmax, &mx[0], 8);
   memcpy(&dmax, &mx[1], 8);
   LAS_CUDA_TRY(cudaMemsetAsync(dG, 0, (size_t)nC * 8, x->stream));
+  if ((st = evaluate(x, C, h, dm1s, dm2, x->dE, x->hG, nullptr)) != LAS_OK) return st;
   if (dmax > 0.0) {
     const double tau = 0.25 * cmax / dmax;
-    const double w[4] = {1.0, -8.0, 8.0, -1.0};
-    const double t[4] = {-2.0, -1.0, 1.0, 2.0};
-    for (int k = 0; k < 4; ++k) {
+    const double w[3] = {6.0, -2.0, -1.0};
+    const double t[3] = {1.0, -1.0, 2.0};
+    for (int k = 0; k < 3; ++k) {
       LAS_CUDA_TRY(cudaMemcpyAsync(x->hCt, C, (size_t)nC * 8, cudaMemcpyDeviceToDevice,
                                    x->stream));
       launch_axpy(x->hCt, x->hdC, t[k] * tau, nC, x->stream);
       if ((st = evaluate(x, x->hCt, h, dm1s, dm2, x->dE, x->hGt, nullptr)) != LAS_OK) return st;
-      launch_axpy(dG, x->hGt, w[k] / (12.0 * tau), nC, x->stream);
+      launch_axpy(dG, x->hGt, w[k] / (6.0 * tau), nC, x->stream);
     }
+    launch_axpy(dG, x->hG, -3.0 / (6.0 * tau), nC, x->stream);
   }
   if (Dg) {
     // Dg = (C X)^T G + C^T dG - transpose  (virtual columns of G and dG are zero)
-    if ((st = evaluate(x, C, h, dm1s, dm2, x->dE, x->hG, nullptr)) != LAS_OK) return st;
     StridedA Ad{x->hdC, 0, 1, nmo};
     StridedA Bg{x->hG, 0, nmo, 1};
     StridedC Cm{x->M, 0, x->op, 1, 1.0, 0};
