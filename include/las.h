@@ -8,10 +8,12 @@
  *     the vectors b^P are stored as packed lower triangles, Naux * Nao(Nao+1)/2 values
  *     (section "Calculation of effective potentials").
  *   - JK call, Eqs. J_1, J_2, K_1, K_2 (Coulomb and exchange matrices of a density).
- *   - AO2MO, Eqs. ao2mo_1, ao2mo_2, ppaa (half and full transforms of b^P and the
- *     (pp|aa)-type integrals).
+ *   - AO2MO, Eqs. ao2mo_1, ao2mo_2, ppaa, papa (half and full transforms of b^P and the
+ *     (pp|aa)- and (pa|pa)-type integrals).
+ *   - Effective embedding and self potentials, Eqs. v_emb and vself.
  *   - LAS wave function, Eq. las_wfn (fragment CAS states times a closed-shell core), its
- *     energy E_LAS = <LAS|H|LAS>, and the orbital gradient whose vanishing is Eq. MO_conv.
+ *     energy E_LAS = <LAS|H|LAS>, the orbital gradient whose vanishing is Eq. MO_conv, and
+ *     the orbital part of the second-order step of Eq. flas (Hessian-vector products).
  *
  * Conventions for every call:
  *   - All arrays are FP64, row-major (C order), and all pointers are DEVICE pointers unless a
@@ -22,8 +24,9 @@
  *     LAS_OK once its work is queued; errors found on the device (a failed bounds or status
  *     check inside a kernel) are recorded in a status word and reported by the next
  *     las_sync() (and by every later call).  The library never aborts and never traps.
- *   - Device memory is allocated only by las_create and freed only by las_destroy; the
- *     evaluation calls allocate nothing.
+ *   - Device memory is allocated by las_create and freed by las_destroy; the energy, gradient,
+ *     transform and JK calls allocate nothing.  The first call of las_frag_ao2mo, las_veff
+ *     and las_orbital_hvp allocates that call's own scratch, kept until las_destroy.
  *   - A context is not thread-safe: use one context per host thread, or serialise calls.
  */
 #ifndef LAS_H_
@@ -66,8 +69,9 @@ typedef struct {
 /* Create a context over the packed Cholesky vectors B_packed (device, naux*nao(nao+1)/2
  * doubles).  In LAS_FP64 mode the context keeps a reference to B_packed, which must stay valid
  * and unchanged until las_destroy.  In LAS_SPLIT_BF16 mode it builds, once, the digit planes of
- * B (owned by the context); afterwards B_packed is read only by las_df_jk, so a caller that
- * never calls las_df_jk may free it after las_create returns.  max_workspace_bytes caps the per-evaluation workspace (0 = choose);
+ * B (owned by the context); afterwards B_packed is read only by the JK calls (las_df_jk,
+ * las_df_jk_density, las_veff: the Coulomb matrix is accumulated over the packed triangle), so
+ * a caller that never makes a JK call may free it after las_create returns.  max_workspace_bytes caps the per-evaluation workspace (0 = choose);
  * the auxiliary index is processed in chunks that fit it.  stream: a cudaStream_t (NULL = the
  * legacy default stream).  Synchronous with respect to the set-up work. */
 las_status las_create(las_ctx** ctx, const las_dims* dims, const double* B_packed,
