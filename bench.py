@@ -225,6 +225,7 @@ def run_ours(args, ws, rank, local):
             las.set_timing(False)
         ms = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
         E_val = float(E.item())
+        G_keep = G.cpu().numpy()
 
         # end to end through the host-buffer C-ABI call (H2D of the step's inputs, D2H of E and
         # dE/dC inside the timed region), pinned host buffers
@@ -283,7 +284,7 @@ def run_ours(args, ws, rank, local):
                 e1.synchronize()
             hvp_ms = e0.elapsed_time(e1)
         las.close()
-        results[prec] = dict(ms_per_step=ms / steps, steps=steps, warmup=warm,
+        results[prec] = dict(G=G_keep, ms_per_step=ms / steps, steps=steps, warmup=warm,
                              evals_per_s=weak_scaling_rate(ws, steps, ms / 1e3),
                              stage_ms=stage_ms, E=E_val,
                              e2e_evals_per_s=weak_scaling_rate(ws, steps, t_e2e), e2e_E=e2e_E,
@@ -558,6 +559,13 @@ def main():
         else None
     batched = run_batched(local) if (ws == 1 and not args.no_batched and
                                      args.precision == "both") else None
+    # split against FP64 on the same inputs (the oracle cannot evaluate this size in seconds;
+    # its parity at this size is tested on auxiliary slices)
+    accuracy = None
+    if all(k in res and "error" not in res[k] for k in ("split", "fp64")):
+        accuracy = {"abs_dE_Eh": abs(res["split"]["E"] - res["fp64"]["E"]),
+                    "max_abs_dG": float(np.abs(res["split"]["G"] - res["fp64"]["G"]).max()),
+                    "max_abs_G": float(np.abs(res["fp64"]["G"]).max())}
     primary = "split" if ("split" in res and "error" not in res["split"]) else "fp64"
     r = res[primary]
     cpu = None
@@ -593,7 +601,7 @@ def main():
             "e2e": {"value": r["e2e_evals_per_s"], "unit": "evals/s",
                     "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
             "gpu_launches": r["launches"], "clocks": r["clocks"], "modes": modes,
-            "frag_ao2mo": ao2mo, "batched": batched,
+            "split_vs_fp64": accuracy, "frag_ao2mo": ao2mo, "batched": batched,
             "input_generation_s": tgen}
     print(json.dumps(line), flush=True)
     if ws > 1:
