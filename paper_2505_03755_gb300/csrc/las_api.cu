@@ -619,7 +619,11 @@ extern "C" las_status las_df_transform(las_ctx* x, const double* C, int p0, int 
     const int nL = std::min(x->Lc, x->X - l0);
     if ((st = half_and_full(x, l0, nL, 0)) != LAS_OK) return st;
     if (Lmu_u) launch_copy_cols(x->Ht, nL, op, n, c, a, Lmu_u + (size_t)l0 * n * a, x->stream);
-    if (Lpu && np > 0) {
+    if (Lpu && np > 0 && x->prec == LAS_SPLIT_BF16) {
+      if ((st = split_lpu(x->split, nL, x->Ht, c, a, C, x->nmo, p0, np,
+                          Lpu + (size_t)l0 * np * a, x->stream)) != LAS_OK)
+        return st;
+    } else if (Lpu && np > 0) {
       // Lpu[b][p][u] = sum_mu C[mu][p0+p] Ht[b][c+u][mu]
       StridedA A{C + p0, 0, 1, x->nmo};
       StridedA B{x->Ht + (size_t)c * n, (long)op * n, 1, n};

@@ -420,6 +420,16 @@ struct RowsStrided {  // element (r, k) = base[r*sr + k*sk] * 2^(gexp ? gexp[k] 
   }
 };
 
+// Row (L, u) of the active columns of the half transform, K = mu: Ht[(L op + c + u) n + mu]
+struct RowsHtAct {
+  const double* Ht;
+  int n, op, c, a;
+  __device__ __forceinline__ double operator()(long r, long k) const {
+    const long L = r / a, u = r - L * a;
+    return Ht[(L * op + c + u) * n + k];
+  }
+};
+
 struct RowsPacked {   // element (r = L*n + mu, k = nu) of the packed symmetric b^L
   const double* Bp;
   long npair;
@@ -904,6 +914,9 @@ struct SplitState {
   int* Wexp;             // [op]
   double* part;          // [ksplit][n][op]
   unsigned long long* mx;  // [op + n] row maxima for long-row slicing
+  Planes Mpd;            // rows p of C[:, p0:p1]^T (K = mu) for the (L|pu) transform (lazy)
+  int* Mpexp;
+  void* Mpblob;
   Planes hdig;           // rows mu of h, K = nu
   int* hexp;             // [n]
   Planes hcdig;          // rows q of (h C_occ)^T, K = mu
@@ -914,6 +927,7 @@ struct SplitState {
 };
 
 static void split_free(SplitState* s) {
+  if (s->Mpblob) cudaFree(s->Mpblob);
   void* ptrs[] = {s->Bdig.p, s->Bexp, s->Cdig.p, s->Cexp, s->Hdig.p, s->Hexp, s->HdigT.p,
                   s->Wdig.p, s->Wexp, s->part, s->mx, s->hdig.p, s->hexp, s->hcdig.p, s->hcexp};
   for (void* q : ptrs)
@@ -1022,6 +1036,42 @@ las_status split_prepare_C(SplitState* s, const double* Cocc, cudaStream_t st) {
   // rows p of C_occ^T (K = nu): element (p, nu) = Cocc[nu*op + p]
   RowsStrided acc{Cocc, 1, s->op, nullptr};
   return slice_rows(acc, s->Cdig, s->Cexp, st, nullptr, true);
+}
+
+las_status split_lpu(SplitState* s, int nL, const double* Ht, int c, int a, const double* C,
+                     int nmo, int p0, int np, double* Lpu, cudaStream_t st) {
+  // Lpu[L][p][u] = sum_mu C[mu][p0+p] Ht[L][c+u][mu]: rows (L,u) of the half transform times the
+  // rows p of C[:, p0:p1]^T, written in the (L, p, u) layout by the half-transform epilogue mode
+  const int n = s->n;
+  if (a < 1 || np < 1) return LAS_OK;
+  if (!s->Mpblob || s->Mpd.R < np) {
+    if (s->Mpblob) cudaFree(s->Mpblob);
+    s->Mpblob = nullptr;
+    const size_t pb = planes_bytes(nmo, n), eb = rup((size_t)nmo * 4, 256);
+    if (cudaMalloc(&s->Mpblob, rup(pb, 256) + eb) != cudaSuccess) {
+      las_record_cuda_error(cudaErrorMemoryAllocation, "cudaMalloc(lpu)", __FILE__, __LINE__);
+      return LAS_ERR_CUDA;
+    }
+    cudaError_t e = cudaMemsetAsync(s->Mpblob, 0, rup(pb, 256) + eb, st);
+    if (e != cudaSuccess) {
+      las_record_cuda_error(e, "cudaMemsetAsync(lpu)", __FILE__, __LINE__);
+      return LAS_ERR_CUDA;
+    }
+    s->Mpd = make_planes(s->Mpblob, nmo, n);
+    s->Mpexp = (int*)((uint8_t*)s->Mpblob + rup(pb, 256));
+  }
+  Planes Mp = s->Mpd;
+  Mp.R = np;
+  las_status rc = slice_rows(RowsStrided{C + p0, 1, nmo, nullptr}, Mp, s->Mpexp, st, nullptr,
+                             true);
+  // the active rows (L,u) of this chunk, sliced into the H digit planes (capacity Lc*op rows)
+  Planes Hd = s->Hdig;
+  Hd.R = (long)nL * a;
+  if (rc == LAS_OK) rc = slice_rows(RowsHtAct{Ht, n, s->op, c, a}, Hd, s->Hexp, st, nullptr, true);
+  if (rc == LAS_OK)
+    rc = ozaki_gemm(Hd, 0, s->Hexp, (long)nL * a, Mp, 0, s->Mpexp, np, n, 1, 1, Lpu, 0, 0, a, np,
+                    s->status, st);
+  return rc;
 }
 
 las_status split_half(SplitState* s, int l0, int nL, int oc, double* Ht, cudaStream_t st) {

@@ -50,3 +50,8 @@ las_status frag_split_prepare_M(FragSplit* f, const double* M, cudaStream_t st);
 las_status frag_split_chunk(SplitState* s, FragSplit* f, int l0, int nL, double* H, double* T,
                             int a0, int ma, double* ppaa, double* papa, double* part,
                             long part_elems, int accumulate, cudaStream_t st);
+
+// (L|pu) of las_df_transform for a chunk: Lpu[L][p][u] = sum_mu C[mu][p0+p] Ht[L][c+u][mu]
+// (C: [n][nmo]; Lpu points at the chunk's first row)
+las_status split_lpu(SplitState* s, int nL, const double* Ht, int c, int a, const double* C,
+                     int nmo, int p0, int np, double* Lpu, cudaStream_t st);

@@ -123,3 +123,30 @@ def test_split_df_jk(name):
     assert np.abs(J.cpu().numpy() - ref["J"]).max() <= 1e-11 * np.abs(ref["J"]).max()
     assert np.abs(K.cpu().numpy() - ref["K"]).max() <= 1e-11 * np.abs(ref["K"]).max()
     las.close()
+
+
+@pytest.mark.parametrize("name,p0,p1", [("ragged", 3, 30), ("cfg0", 0, 48), ("nmo_lt_nao", 5, 30)])
+def test_split_df_transform(name, p0, p1):
+    """(L|mu u) and (L|pu) (Eqs. ao2mo_1, ao2mo_2) in split precision, p over a ragged range."""
+    s = SMALL[name]()
+    las = make_las(s, "split")
+    a0, a1 = s.ncore, s.ncore + s.nactive
+    lmu, lpu = las.df_transform(dev(s.C), p0, p1)
+    las.sync()
+    rmu, rpu = O.df_transform(s.Bp, s.nao, s.C, (a0, a1), p0, p1)
+    assert np.abs(lmu.cpu().numpy() - rmu).max() <= 1e-11 * np.abs(rmu).max()
+    assert np.abs(lpu.cpu().numpy() - rpu).max() <= 1e-11 * np.abs(rpu).max()
+    las.close()
+
+
+def test_split_df_transform_chunked_config1():
+    """config1 (Nao=400) with a workspace cap that splits the auxiliary index into chunks."""
+    s = config_system(1)
+    las = make_las(s, "split", max_workspace_bytes=256 << 20)
+    a0, a1 = s.ncore, s.ncore + s.nactive
+    lmu, lpu = las.df_transform(dev(s.C), 0, s.nmo)
+    las.sync()
+    rmu, rpu = O.df_transform(s.Bp, s.nao, s.C, (a0, a1), 0, s.nmo)
+    assert np.abs(lmu.cpu().numpy() - rmu).max() <= 1e-11 * np.abs(rmu).max()
+    assert np.abs(lpu.cpu().numpy() - rpu).max() <= 1e-11 * np.abs(rpu).max()
+    las.close()
