@@ -313,6 +313,57 @@ def energy_grad_batched(problems, items, stream=None):
     _check(lib.las_energy_grad_batched(n, arr, its, st), "las_energy_grad_batched")
 
 
+def aux_range(naux: int, rank: int, world: int) -> tuple[int, int]:
+    """The contiguous block [l0, l1) of auxiliary indices that `rank` of `world` owns when the
+    evaluation is partitioned along L (blocks differ in size by at most one row, in rank order)."""
+    if world < 1 or not 0 <= rank < world or naux < 0:
+        raise ValueError("need 0 <= rank < world and naux >= 0")
+    q, r = divmod(naux, world)
+    l0 = rank * q + min(rank, r)
+    return l0, l0 + q + (1 if rank < r else 0)
+
+
+def _aligned(k: int) -> int:
+    return (k + 31) // 32 * 32
+
+
+def aux_shard_partial(las, C, h, dm1s, dm2, rank: int, want_gorb: bool = False):
+    """One rank's share of the energy and gradient when its context holds only its block of
+    auxiliary rows of B (see `aux_range`).
+
+    Every two-electron piece of the energy and of the gradient is a sum over L of per-L terms
+    (v_L, T_L, Y_L, H_L; Eqs. J_1, K_1, ao2mo_1, ao2mo_2) and the one-electron matrix enters both
+    linearly, so rank 0 alone passes h and the others a zero matrix: the ranks' shares then add
+    up to the whole system's E, dE/dC and rotation gradient.  Returns (buf, E, G, g): the shares
+    are views into the one flat device buffer `buf` (dE/dC, g, E at 256-byte-aligned offsets,
+    zero padding between them), so a single sum over ranks of `buf` completes the evaluation."""
+    import torch
+    n, nmo = C.shape
+    offg = _aligned(n * nmo)
+    offE = offg + (_aligned(nmo * nmo) if want_gorb else 0)
+    buf = torch.zeros(offE + 1, dtype=torch.float64, device=C.device)
+    G = buf[:n * nmo].view(n, nmo)
+    g = buf[offg:offg + nmo * nmo].view(nmo, nmo) if want_gorb else None
+    E = buf[offE]
+    hl = h if rank == 0 else torch.zeros_like(h)
+    las.energy_grad(C, hl, dm1s, dm2, want_gorb=want_gorb, E=E, G=G, g=g)
+    return buf, E, G, g
+
+
+def energy_grad_aux_sharded(las, C, h, dm1s, dm2, want_gorb: bool = False, group=None):
+    """E and dE/dC (and the rotation gradient) of the whole system, L-partitioned over the ranks
+    of `group`: each rank evaluates its share (`aux_shard_partial`) and one all-reduce (sum) of
+    the shares' flat buffer completes the evaluation on every rank.  Without an initialised
+    process group (or with one rank) this is the plain single-context evaluation."""
+    import torch.distributed as dist
+    ws = dist.get_world_size(group) if dist.is_available() and dist.is_initialized() else 1
+    rank = dist.get_rank(group) if ws > 1 else 0
+    buf, E, G, g = aux_shard_partial(las, C, h, dm1s, dm2, rank, want_gorb)
+    if ws > 1:
+        dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
+    return (E, G, g) if want_gorb else (E, G)
+
+
 def split_gemm(A, B, out=None, stream=None):
     """C = A @ B (float64 CUDA tensors) through the emulated-FP64 BF16 tensor-core GEMM."""
     import torch
