@@ -75,6 +75,7 @@ struct las_ctx {
   // fragment AO2MO workspace (allocated by the first las_frag_ao2mo call)
   double *fH, *fT, *fpart;
   long fLc, fpart_elems;
+  size_t fbytes;   // device bytes of the fragment AO2MO workspace (counted in `bytes`)
   int fnmo, fma;
   FragSplit* fsplit;
   double *vJ, *vK;   // scratch of las_veff (allocated by its first call)
@@ -621,7 +622,7 @@ extern "C" las_status las_df_transform(las_ctx* x, const double* C, int p0, int 
     if (Lmu_u) launch_copy_cols(x->Ht, nL, op, n, c, a, Lmu_u + (size_t)l0 * n * a, x->stream);
     if (Lpu && np > 0 && x->prec == LAS_SPLIT_BF16) {
       if ((st = split_lpu(x->split, nL, x->Ht, c, a, C, x->nmo, p0, np,
-                          Lpu + (size_t)l0 * np * a, x->stream)) != LAS_OK)
+                          Lpu + (size_t)l0 * np * a, x->stream, &x->bytes)) != LAS_OK)
         return st;
     } else if (Lpu && np > 0) {
       // Lpu[b][p][u] = sum_mu C[mu][p0+p] Ht[b][c+u][mu]
@@ -784,14 +785,18 @@ static las_status frag_workspace(las_ctx* x, int ma) {
   }
   if (x->fsplit) frag_split_destroy(x->fsplit);
   x->fsplit = nullptr;
+  x->bytes -= x->fbytes;
+  x->fbytes = 0;
+  x->fLc = 0;
+  const size_t bytes0 = x->bytes;
   las_status st = LAS_OK;
-  if ((st = dalloc(x, (void**)&x->fH, sizeof(double) * (size_t)Lc * nmo * n)) != LAS_OK ||
-      (st = dalloc(x, (void**)&x->fT, sizeof(double) * (size_t)Lc * n2)) != LAS_OK ||
-      (st = dalloc(x, (void**)&x->fpart, sizeof(double) * (size_t)part)) != LAS_OK)
-    return st;
-  if (x->prec == LAS_SPLIT_BF16 &&
-      (st = frag_split_create(&x->fsplit, n, nmo, ma, Lc, x->stream, &x->bytes)) != LAS_OK)
-    return st;
+  if ((st = dalloc(x, (void**)&x->fH, sizeof(double) * (size_t)Lc * nmo * n)) == LAS_OK &&
+      (st = dalloc(x, (void**)&x->fT, sizeof(double) * (size_t)Lc * n2)) == LAS_OK &&
+      (st = dalloc(x, (void**)&x->fpart, sizeof(double) * (size_t)part)) == LAS_OK &&
+      x->prec == LAS_SPLIT_BF16)
+    st = frag_split_create(&x->fsplit, n, nmo, ma, Lc, x->stream, &x->bytes);
+  x->fbytes = x->bytes - bytes0;   // also what a failed attempt left allocated
+  if (st != LAS_OK) return st;
   x->fLc = Lc;
   x->fnmo = nmo;
   x->fma = ma;

@@ -1039,19 +1039,20 @@ las_status split_prepare_C(SplitState* s, const double* Cocc, cudaStream_t st) {
 }
 
 las_status split_lpu(SplitState* s, int nL, const double* Ht, int c, int a, const double* C,
-                     int nmo, int p0, int np, double* Lpu, cudaStream_t st) {
+                     int nmo, int p0, int np, double* Lpu, cudaStream_t st, size_t* bytes) {
   // Lpu[L][p][u] = sum_mu C[mu][p0+p] Ht[L][c+u][mu]: rows (L,u) of the half transform times the
   // rows p of C[:, p0:p1]^T, written in the (L, p, u) layout by the half-transform epilogue mode
   const int n = s->n;
   if (a < 1 || np < 1) return LAS_OK;
-  if (!s->Mpblob || s->Mpd.R < np) {
-    if (s->Mpblob) cudaFree(s->Mpblob);
-    s->Mpblob = nullptr;
+  if (np > nmo) return LAS_ERR_INTERNAL;
+  if (!s->Mpblob) {   // planes for all nmo rows of C^T: allocated once per context
     const size_t pb = planes_bytes(nmo, n), eb = rup((size_t)nmo * 4, 256);
     if (cudaMalloc(&s->Mpblob, rup(pb, 256) + eb) != cudaSuccess) {
+      s->Mpblob = nullptr;
       las_record_cuda_error(cudaErrorMemoryAllocation, "cudaMalloc(lpu)", __FILE__, __LINE__);
       return LAS_ERR_CUDA;
     }
+    *bytes += rup(pb, 256) + eb;
     cudaError_t e = cudaMemsetAsync(s->Mpblob, 0, rup(pb, 256) + eb, st);
     if (e != cudaSuccess) {
       las_record_cuda_error(e, "cudaMemsetAsync(lpu)", __FILE__, __LINE__);

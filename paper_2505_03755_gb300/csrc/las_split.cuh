@@ -52,6 +52,7 @@ las_status frag_split_chunk(SplitState* s, FragSplit* f, int l0, int nL, double*
                             long part_elems, int accumulate, cudaStream_t st);
 
 // (L|pu) of las_df_transform for a chunk: Lpu[L][p][u] = sum_mu C[mu][p0+p] Ht[L][c+u][mu]
-// (C: [n][nmo]; Lpu points at the chunk's first row)
+// (C: [n][nmo]; Lpu points at the chunk's first row).  The digit planes of C^T are allocated on
+// the first call and their size is added to *bytes.
 las_status split_lpu(SplitState* s, int nL, const double* Ht, int c, int a, const double* C,
-                     int nmo, int p0, int np, double* Lpu, cudaStream_t st);
+                     int nmo, int p0, int np, double* Lpu, cudaStream_t st, size_t* bytes);

@@ -96,3 +96,37 @@ def test_frag_ao2mo_active_range_edges(precision, tol, a0, ma):
     assert np.abs(ppaa.cpu().numpy() - ppaa_r).max() <= tol * np.abs(ppaa_r).max()
     assert np.abs(papa.cpu().numpy() - papa_r).max() <= tol * np.abs(papa_r).max()
     las.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_device_bytes_follow_workspace_growth(precision):
+    """Growing the fragment workspace (ma 2 -> 4) leaves the context owning what a fresh context
+    that only ran ma = 4 owns (freed buffers are no longer counted); a call that fits adds
+    nothing; the transform's digit planes are counted once, on the first split-mode call."""
+    torch_cuda()
+    built()
+    from paper_2505_03755_gb300 import LasDF
+    s, M = _case(96, 200, 905)
+    Md = dev(M)
+    grown = LasDF(dev(s.Bp), s.nao, s.naux, s.nmo, s.ncore, s.nact, precision=precision)
+    fresh = LasDF(dev(s.Bp), s.nao, s.naux, s.nmo, s.ncore, s.nact, precision=precision)
+    b0 = grown.device_bytes()
+    assert fresh.device_bytes() == b0
+    grown.frag_ao2mo(Md, 10, 2)
+    grown.frag_ao2mo(Md, 10, 4)
+    fresh.frag_ao2mo(Md, 10, 4)
+    grown.sync()
+    fresh.sync()
+    assert grown.device_bytes() == fresh.device_bytes() > b0
+    grown.frag_ao2mo(Md, 10, 3)
+    assert grown.device_bytes() == fresh.device_bytes()
+    C = dev(s.C)
+    b1 = grown.device_bytes()
+    grown.df_transform(C, 0, s.nmo)
+    b2 = grown.device_bytes()
+    grown.df_transform(C, 0, s.nmo)
+    grown.sync()
+    assert grown.device_bytes() == b2
+    assert (b2 > b1) == (precision == "split")
+    grown.close()
+    fresh.close()
