@@ -24,9 +24,11 @@
  *     LAS_OK once its work is queued; errors found on the device (a failed bounds or status
  *     check inside a kernel) are recorded in a status word and reported by the next
  *     las_sync() (and by every later call).  The library never aborts and never traps.
- *   - Device memory is allocated by las_create and freed by las_destroy; the energy, gradient,
- *     transform and JK calls allocate nothing.  The first call of las_frag_ao2mo, las_veff
- *     and las_orbital_hvp allocates that call's own scratch, kept until las_destroy.
+ *   - Device memory is allocated by las_create and freed by las_destroy; the energy, gradient
+ *     and JK calls allocate nothing.  The first call of las_frag_ao2mo, las_veff and
+ *     las_orbital_hvp, and in LAS_SPLIT_BF16 mode the first las_df_transform that asks for
+ *     Lpu, allocates that call's own scratch, kept until las_destroy (las_frag_ao2mo grows
+ *     its scratch when a later call needs more, after waiting for the context's stream).
  *   - A context is not thread-safe: use one context per host thread, or serialise calls.
  */
 #ifndef LAS_H_
@@ -71,9 +73,14 @@ typedef struct {
  * and unchanged until las_destroy.  In LAS_SPLIT_BF16 mode it builds, once, the digit planes of
  * B (owned by the context); afterwards B_packed is read only by the JK calls (las_df_jk,
  * las_df_jk_density, las_veff: the Coulomb matrix is accumulated over the packed triangle), so
- * a caller that never makes a JK call may free it after las_create returns.  max_workspace_bytes caps the per-evaluation workspace (0 = choose);
- * the auxiliary index is processed in chunks that fit it.  stream: a cudaStream_t (NULL = the
- * legacy default stream).  Synchronous with respect to the set-up work. */
+ * a caller that never makes a JK call may free it after las_create returns.
+ * max_workspace_bytes caps the per-evaluation workspace (0 = choose); the auxiliary index is
+ * processed in chunks that fit it.  stream: a cudaStream_t (NULL = the legacy default stream).
+ * Synchronous with respect to the set-up work.
+ * B_packed may hold any block of auxiliary rows (dims->naux of them): every two-electron term of
+ * the energy and of its gradients is a sum over L, so the results of contexts over disjoint
+ * blocks that together cover the auxiliary index add up to the whole system's, provided that
+ * exactly one of them is passed the one-electron matrix h and the others a zero matrix. */
 las_status las_create(las_ctx** ctx, const las_dims* dims, const double* B_packed,
                       las_precision precision, size_t max_workspace_bytes, void* stream);
 
@@ -91,7 +98,10 @@ size_t las_device_bytes(const las_ctx* ctx);
 /* AO2MO half and full transforms (Eqs. ao2mo_1, ao2mo_2) over the active orbitals u:
  *   Lmu_u[L][mu][u] = sum_nu b^L_{mu nu} C[nu][ncore+u]            (naux x nao x nact_total)
  *   Lpu[L][p-p0][u] = sum_mu C[mu][p] Lmu_u[L][mu][u],  p in [p0,p1) (naux x (p1-p0) x nact_total)
- * C: device [nao][nmo].  Either output may be NULL.  0 <= p0 <= p1 <= nmo. */
+ * C: device [nao][nmo].  Either output may be NULL.  0 <= p0 <= p1 <= nmo.
+ * In LAS_SPLIT_BF16 mode both products are split-precision GEMMs: the second takes the rows
+ * (L, u) of the half transform and the rows p of C^T as digit planes and writes Lpu in the
+ * layout above directly from the GEMM epilogue. */
 las_status las_df_transform(las_ctx* ctx, const double* C, int p0, int p1, double* Lmu_u,
                             double* Lpu);
 
