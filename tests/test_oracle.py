@@ -440,3 +440,61 @@ def test_planted_mistakes(cfg0, monkeypatch):
     monkeypatch.setattr(O, "energy_grad", bad_grad)
     assert _fd_check(s, 3) > 1e-3
     monkeypatch.setattr(O, "energy_grad", orig_eg)
+
+
+@pytest.fixture(scope="module")
+def many_blocks():
+    # 517 auxiliary rows: the oracle's blocks along P (at most 240, the paper's N_blk) are
+    # 240 + 240 + 37, so every blocked sum crosses two block edges and ends on a ragged block
+    return make_system(11, 517, 2, [(2, 2), (2, 3)], seed=2024)
+
+
+def test_blocking_over_P(many_blocks):
+    """The blocked Tier B sums against unblocked definitions, with several blocks along P."""
+    s = many_blocks
+    n = s.nao
+    assert O.block_size(n, s.naux) == 240 and s.naux % 240 != 0
+    r = O.system_energy_grad(s)
+    # energy: Tier A builds (pq|rs) from all of B at once
+    ea = O.energy_tier_a(s.Bp, n, s.h, s.C, s.ncore, s.dm1s, s.dm2)
+    assert abs(r["E"] - ea) < 1e-12 * abs(ea)
+    # J and K against the 4-index integrals
+    eri = O.ao_eri(s.Bp, n)
+    rng = np.random.default_rng(3)
+    D = rng.standard_normal((n, n))
+    D = D + D.T
+    (J,), (K,) = O.df_jk(s.Bp, n, [D])
+    assert np.abs(J - np.einsum("mnls,ls->mn", eri, D)).max() < 1e-11
+    assert np.abs(K - np.einsum("mlsn,ls->mn", eri, D)).max() < 1e-11
+    # active integrals against the unblocked MO transform
+    a = s.nactive
+    C_a = s.C[:, s.ncore:s.ncore + a]
+    e_act, _ = O.ao2mo_active(s.Bp, n, C_a)
+    assert np.abs(e_act - O.mo_eri(s.Bp, n, C_a)).max() < 1e-12 * np.abs(e_act).max()
+    # gradient: central differences
+    assert _fd_check(s, 4) < 1e-6
+    # slices of the auxiliary index that start and end inside blocks add up to the whole
+    # (the one-electron matrix in one slice only)
+    parts = [(0, 100, s.h), (100, 250, 0 * s.h), (250, 517, 0 * s.h)]
+    tot_E, tot_G = 0.0, 0.0
+    for l0, l1, h in parts:
+        p = O.energy_grad(s.Bp, n, h, s.C, s.ncore, s.dm1s, s.dm2, l0=l0, l1=l1)
+        tot_E += p["E"]
+        tot_G = tot_G + p["G"]
+    assert abs(tot_E - r["E"]) < 1e-12 * abs(r["E"])
+    assert np.abs(tot_G - r["G"]).max() < 1e-12 * np.abs(r["G"]).max()
+
+
+def test_planted_dropped_ragged_block(many_blocks, monkeypatch):
+    """A blocked loop that drops its last, ragged block must fail the pin above."""
+    s = many_blocks
+    ea = O.energy_tier_a(s.Bp, s.nao, s.h, s.C, s.ncore, s.dm1s, s.dm2)
+    orig = O.p_blocks
+
+    def bad_blocks(Bp, n, l0=0, l1=None, nblk=240):
+        for a, b, blk in orig(Bp, n, l0, l1, nblk):
+            if b - a == 240:
+                yield a, b, blk
+
+    monkeypatch.setattr(O, "p_blocks", bad_blocks)
+    assert abs(O.system_energy_grad(s, with_grad=False)["E"] - ea) > 1e-6 * abs(ea)
