@@ -123,6 +123,20 @@ def _ptr(t) -> int | None:
     return t.data_ptr()
 
 
+def _shape_check(t, shape, name: str) -> None:
+    """Raise ValueError unless t (a tensor or array) has exactly `shape` (a tuple of ints) or,
+    for a flat buffer, `shape` is an int and t holds that many elements.  The library cannot see
+    the size of a device buffer, so this is what keeps a wrong argument from being read or
+    written past its end."""
+    got = tuple(t.shape)
+    if isinstance(shape, int):
+        n = int(np.prod(got)) if got else 1
+        if n != shape:
+            raise ValueError(f"{name}: expected {shape} elements, got shape {got}")
+    elif got != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {got}")
+
+
 def _hptr(a) -> int | None:
     if a is None:
         return None
@@ -159,6 +173,27 @@ class LasDF:
     def stream(self):
         return self._stream
 
+    @property
+    def nact_total(self) -> int:
+        return sum(self.nact)
+
+    def _arg(self, t, shape, name: str) -> int | None:
+        """Device pointer of t after checking its shape and that it lives on the context's
+        device (None passes through: the library checks which arguments are required)."""
+        if t is None:
+            return None
+        _shape_check(t, shape, name)
+        p = _ptr(t)
+        if t.device != self._B.device:
+            raise ValueError(f"{name}: on {t.device}, the context is on {self._B.device}")
+        return p
+
+    def _state_args(self, C, h, dm1s, dm2):
+        n, nmo = self.nao, self.nmo
+        return (self._arg(C, (n, nmo), "C"), self._arg(h, (n, n), "h"),
+                self._arg(dm1s, sum(2 * m * m for m in self.nact), "dm1s"),
+                self._arg(dm2, sum(m ** 4 for m in self.nact), "dm2"))
+
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.las_destroy(self._h)
@@ -188,8 +223,8 @@ class LasDF:
         import torch
         if E is None:
             E = torch.empty((), dtype=torch.float64, device=C.device)
-        _check(self._lib.las_energy(self._h, _ptr(C), _ptr(h), _ptr(dm1s), _ptr(dm2), _ptr(E)),
-               "las_energy")
+        _check(self._lib.las_energy(self._h, *self._state_args(C, h, dm1s, dm2),
+                                    self._arg(E, 1, "E")), "las_energy")
         return E
 
     def energy_grad(self, C, h, dm1s, dm2, want_gorb: bool = False, E=None, G=None, g=None):
@@ -201,13 +236,22 @@ class LasDF:
             G = torch.empty((self.nao, self.nmo), dtype=torch.float64, device=dev)
         if want_gorb and g is None:
             g = torch.empty((self.nmo, self.nmo), dtype=torch.float64, device=dev)
-        _check(self._lib.las_energy_grad(self._h, _ptr(C), _ptr(h), _ptr(dm1s), _ptr(dm2),
-                                         _ptr(E), _ptr(G), _ptr(g)), "las_energy_grad")
+        _check(self._lib.las_energy_grad(self._h, *self._state_args(C, h, dm1s, dm2),
+                                         self._arg(E, 1, "E"),
+                                         self._arg(G, (self.nao, self.nmo), "G"),
+                                         self._arg(g, (self.nmo, self.nmo), "g")),
+               "las_energy_grad")
         return (E, G, g) if want_gorb else (E, G)
 
     def energy_grad_host(self, C, h, dm1s, dm2, with_grad: bool = True):
         E = np.zeros(1)
         G = np.empty((self.nao, self.nmo)) if with_grad else None
+        n = self.nao
+        for t, shape, name in ((C, (n, self.nmo), "C"), (h, (n, n), "h"),
+                               (dm1s, sum(2 * m * m for m in self.nact), "dm1s"),
+                               (dm2, sum(m ** 4 for m in self.nact), "dm2")):
+            if t is not None:
+                _shape_check(t, shape, name)
         _check(self._lib.las_energy_grad_host(self._h, _hptr(C), _hptr(h), _hptr(dm1s),
                                               _hptr(dm2), _hptr(E), _hptr(G)),
                "las_energy_grad_host")
@@ -218,15 +262,17 @@ class LasDF:
         import torch
         E = torch.empty((), dtype=torch.float64, device=C.device)
         G = torch.empty((self.nao, self.nmo), dtype=torch.float64, device=C.device)
-        _check(self._lib.las_autotune(self._h, _ptr(C), _ptr(h), _ptr(dm1s), _ptr(dm2),
-                                      _ptr(E), _ptr(G)), "las_autotune")
+        _check(self._lib.las_autotune(self._h, *self._state_args(C, h, dm1s, dm2), _ptr(E),
+                                      _ptr(G)), "las_autotune")
 
     def df_jk(self, C, J=None, K=None):
         import torch
         n = self.nao
         J = torch.empty((n, n), dtype=torch.float64, device=C.device) if J is None else J
         K = torch.empty((n, n), dtype=torch.float64, device=C.device) if K is None else K
-        _check(self._lib.las_df_jk(self._h, _ptr(C), _ptr(J), _ptr(K)), "las_df_jk")
+        _check(self._lib.las_df_jk(self._h, self._arg(C, (n, self.nmo), "C"),
+                                   self._arg(J, (n, n), "J"), self._arg(K, (n, n), "K")),
+               "las_df_jk")
         return J, K
 
     def df_jk_density(self, Cx, w, J=None, K=None):
@@ -235,8 +281,13 @@ class LasDF:
         n = self.nao
         J = torch.empty((n, n), dtype=torch.float64, device=Cx.device) if J is None else J
         K = torch.empty((n, n), dtype=torch.float64, device=Cx.device) if K is None else K
-        _check(self._lib.las_df_jk_density(self._h, _ptr(Cx), _ptr(w), int(Cx.shape[1]),
-                                           _ptr(J), _ptr(K)), "las_df_jk_density")
+        if Cx.dim() != 2:
+            raise ValueError("Cx must be nao x r")
+        r = int(Cx.shape[1])
+        _check(self._lib.las_df_jk_density(self._h, self._arg(Cx, (n, r), "Cx"),
+                                           self._arg(w, (r,), "w"), r,
+                                           self._arg(J, (n, n), "J"), self._arg(K, (n, n), "K")),
+               "las_df_jk_density")
         return J, K
 
     def orbital_hvp(self, C, h, dm1s, dm2, X, want_Dg: bool = True):
@@ -247,8 +298,9 @@ class LasDF:
         dG = torch.empty((self.nao, self.nmo), dtype=torch.float64, device=dev)
         Dg = torch.empty((self.nmo, self.nmo), dtype=torch.float64, device=dev) if want_Dg \
             else None
-        _check(self._lib.las_orbital_hvp(self._h, _ptr(C), _ptr(h), _ptr(dm1s), _ptr(dm2),
-                                         _ptr(X), _ptr(dG), _ptr(Dg)), "las_orbital_hvp")
+        _check(self._lib.las_orbital_hvp(self._h, *self._state_args(C, h, dm1s, dm2),
+                                         self._arg(X, (self.nmo, self.nmo), "X"), _ptr(dG),
+                                         _ptr(Dg)), "las_orbital_hvp")
         return dG, Dg
 
     def veff(self, C_alpha, w_alpha, C_beta, w_beta):
@@ -258,9 +310,14 @@ class LasDF:
         n, dev = self.nao, C_alpha.device
         va = torch.empty((n, n), dtype=torch.float64, device=dev)
         vb = torch.empty((n, n), dtype=torch.float64, device=dev)
-        _check(self._lib.las_veff(self._h, _ptr(C_alpha), _ptr(w_alpha), int(C_alpha.shape[1]),
-                                  _ptr(C_beta), _ptr(w_beta), int(C_beta.shape[1]), _ptr(va),
-                                  _ptr(vb)), "las_veff")
+        if C_alpha.dim() != 2 or C_beta.dim() != 2:
+            raise ValueError("C_alpha and C_beta must be nao x r")
+        ra, rb = int(C_alpha.shape[1]), int(C_beta.shape[1])
+        _check(self._lib.las_veff(self._h, self._arg(C_alpha, (n, ra), "C_alpha"),
+                                  self._arg(w_alpha, (ra,), "w_alpha"), ra,
+                                  self._arg(C_beta, (n, rb), "C_beta"),
+                                  self._arg(w_beta, (rb,), "w_beta"), rb, _ptr(va), _ptr(vb)),
+               "las_veff")
         return va, vb
 
     def frag_ao2mo(self, M, a0: int, ma: int, want_ppaa: bool = True, want_papa: bool = True):
@@ -273,20 +330,22 @@ class LasDF:
             if want_ppaa else None
         papa = torch.empty((nmo, ma, nmo, ma), dtype=torch.float64, device=dev) \
             if want_papa else None
-        _check(self._lib.las_frag_ao2mo(self._h, _ptr(M), int(a0), int(ma), _ptr(ppaa),
-                                        _ptr(papa)), "las_frag_ao2mo")
+        _check(self._lib.las_frag_ao2mo(self._h, self._arg(M, (self.nao, nmo), "M"), int(a0),
+                                        int(ma), _ptr(ppaa), _ptr(papa)), "las_frag_ao2mo")
         return ppaa, papa
 
     def df_transform(self, C, p0: int, p1: int, want_lmu: bool = True, want_lpu: bool = True):
         import torch
+        if not 0 <= p0 <= p1 <= self.nmo:
+            raise ValueError("need 0 <= p0 <= p1 <= nmo")
         a = sum(self.nact)
         dev = C.device
         lmu = torch.empty((self.naux, self.nao, a), dtype=torch.float64, device=dev) \
             if want_lmu else None
         lpu = torch.empty((self.naux, p1 - p0, a), dtype=torch.float64, device=dev) \
             if want_lpu else None
-        _check(self._lib.las_df_transform(self._h, _ptr(C), p0, p1, _ptr(lmu), _ptr(lpu)),
-               "las_df_transform")
+        _check(self._lib.las_df_transform(self._h, self._arg(C, (self.nao, self.nmo), "C"), p0,
+                                          p1, _ptr(lmu), _ptr(lpu)), "las_df_transform")
         return lmu, lpu
 
 
@@ -308,7 +367,13 @@ def energy_grad_batched(problems, items, stream=None):
     lib = load_library()
     n = len(problems)
     arr = (ctypes.c_void_p * n)(*[p._h.value for p in problems])
-    its = (BatchItem * n)(*[BatchItem(*[_ptr(t) for t in it]) for it in items])
+    if len(items) != n:
+        raise ValueError("one item per problem")
+    rows = []
+    for p, (C, h, dm1s, dm2, E, G) in zip(problems, items):
+        rows.append(BatchItem(*p._state_args(C, h, dm1s, dm2), p._arg(E, 1, "E"),
+                              p._arg(G, (p.nao, p.nmo), "dEdC")))
+    its = (BatchItem * n)(*rows)
     st = (stream or torch.cuda.current_stream()).cuda_stream
     _check(lib.las_energy_grad_batched(n, arr, its, st), "las_energy_grad_batched")
 
@@ -373,6 +438,7 @@ def split_gemm(A, B, out=None, stream=None):
     if K2 != K:
         raise ValueError("inner dimensions differ")
     C = torch.empty((M, N), dtype=torch.float64, device=A.device) if out is None else out
+    _shape_check(C, (M, N), "out")
     nbytes = int(lib.las_split_gemm_workspace(M, N, K))
     ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=A.device)
     st = (stream or torch.cuda.current_stream()).cuda_stream

@@ -35,3 +35,24 @@ def test_status_strings():
     lib = load_library()
     for code in range(7):
         assert lib.las_status_str(code)
+
+
+def test_binding_shape_checks():
+    """The binding rejects a buffer of the wrong shape before any pointer reaches the library
+    (which cannot see the size of a device buffer)."""
+    import numpy as np
+    import pytest
+    import torch
+    from paper_2505_03755_gb300.las import _shape_check
+    _shape_check(torch.zeros(4, 3, dtype=torch.float64), (4, 3), "C")
+    _shape_check(torch.zeros(2, 2, 2, dtype=torch.float64), 8, "dm1s")   # flat count
+    _shape_check(torch.zeros((), dtype=torch.float64), 1, "E")
+    _shape_check(np.zeros((5, 5)), (5, 5), "h")
+    with pytest.raises(ValueError):
+        _shape_check(torch.zeros(3, 4, dtype=torch.float64), (4, 3), "C")     # transposed
+    with pytest.raises(ValueError):
+        _shape_check(torch.zeros(4, 2, dtype=torch.float64), (4, 3), "G")     # too small
+    with pytest.raises(ValueError):
+        _shape_check(torch.zeros(7, dtype=torch.float64), 8, "dm2")
+    with pytest.raises(ValueError):
+        _shape_check(torch.zeros(12, dtype=torch.float64), (4, 3), "C")       # flat for a matrix

@@ -67,6 +67,32 @@ def test_invalid_arguments():
         LasDF(dev(s.Bp), s.nao, s.naux, s.nmo, s.ncore, [2, 0])  # empty fragment
 
 
+def test_wrong_shapes_are_rejected_before_launch():
+    """Transposed or short buffers raise ValueError in the binding; the context still works."""
+    torch = torch_cuda()
+    s = SMALL["nmo_lt_nao"]()
+    ref = O.system_energy_grad(s)
+    las = make_las(s)
+    C, h = dev(s.C), dev(s.h)
+    dm1s, dm2 = dev(s.dm1s_flat()), dev(s.dm2_flat())
+    with pytest.raises(ValueError):
+        las.energy_grad(C.T.contiguous(), h, dm1s, dm2)                      # transposed C
+    with pytest.raises(ValueError):
+        las.energy_grad(C, h, dm1s, dm2, G=torch.empty((s.nao, s.nmo - 1), dtype=torch.float64,
+                                                      device="cuda:0"))      # short output
+    with pytest.raises(ValueError):
+        las.energy_grad(C, h, dm1s, dm2[:-1])                                 # short 2-RDM
+    with pytest.raises(ValueError):
+        las.df_jk(C[:, :5].contiguous())
+    with pytest.raises(ValueError):
+        las.df_transform(C, 3, 2)
+    E, G = las.energy_grad(C, h, dm1s, dm2)
+    las.sync()
+    assert abs(float(E) - ref["E"]) <= E_REL * max(1.0, abs(ref["E"]))
+    assert np.abs(G.cpu().numpy() - ref["G"]).max() <= G_ABS
+    las.close()
+
+
 def test_host_entry_point_matches_device():
     s = SMALL["ragged"]()
     E0, G0, _ = gpu_energy_grad(s, "fp64")
