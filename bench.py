@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(config="nao1200_naux4800_core150_act22e40o_5frag", nao=1200, naux=4800,
                 ncore=150, frags=[(6, 8)] + [(4, 8)] * 4)
 METRIC = "LAS energy+gradient evals/s at Nao=1200 (FP64 vs split-prec), % of roofline"
-FP64_NOMINAL_TFLOPS = 1.25      # recipe nominal FP64 (DFMA/DMMA) for GB300
+FP64_NOMINAL_TFLOPS = 1.25      # nominal FP64 (DFMA/DMMA) rate of GB300
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -60,8 +60,8 @@ def weak_scaling_rate(ws: int, steps: int, seconds: float) -> float:
 
 def rank_seed(rank: int) -> int:
     """Independent problems per rank: the Nao=1200 system drawn with a rank-specific seed."""
-    from las_inputs import BASE_SEED
-    return BASE_SEED + 2 + 1000 * rank
+    from las_inputs import WORKLOADS
+    return WORKLOADS["nao1200"]["seed"] + 1000 * rank
 
 
 def dist_env():
@@ -139,7 +139,7 @@ def algorithmic_work(nao, naux, ncore, nact):
 
 
 def make_inputs(rank: int):
-    from las_inputs import BASE_SEED, make_system
+    from las_inputs import make_system
     w = WORKLOAD
     t0 = time.time()
     s = make_system(w["nao"], w["naux"], w["ncore"], w["frags"], seed=rank_seed(rank))
@@ -193,7 +193,7 @@ def run_ours(args, ws, rank, local):
         warm = args.warmup if prec == precs[0] else max(1, min(args.warmup, args.fp64_warmup))
         try:
             las = LasDF(Bd, s.nao, s.naux, s.nmo, s.ncore, s.nact, precision=prec, stream=stream)
-        except Exception as e:  # a mode this build does not provide
+        except Exception as e:  # a precision mode the library does not provide
             results[prec] = {"error": str(e)}
             continue
         E = torch.empty((), dtype=torch.float64, device=dev)
@@ -326,14 +326,14 @@ def roofline_for(prec, r, work, peaks, s):
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_ozaki (half transform, tcgen05 BF16 digit products)",
                 "peak_source": "bf16_tflops_sustained of MEASURED_PEAKS.json (of measured)"
-                if peaks.get("bf16_tflops_sustained") else "recipe fallback (sustained)",
+                if peaks.get("bf16_tflops_sustained") else "of fallback (1.7 PFLOP/s sustained)",
                 "algorithmic_flops": flops}
     if prec == "fp64":
         achieved = work["s1"] / t_s1 / 1e12
         return {"bound": "tensor", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
                 "kernel": "k_gemm_f64 (half transform, DMMA)",
-                "peak_source": "nominal FP64 of the recipe (no measured FP64 peak in "
+                "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in "
                                "MEASURED_PEAKS.json)"}
     return None
 
@@ -434,13 +434,13 @@ def run_batched(local: int, reps: int = 5) -> dict:
 def cpu_baseline(sample_rows: int):
     """The oracle as it stands, on auxiliary rows [0, sample_rows) of the same workload,
     scaled to a full evaluation."""
-    from las_inputs import BASE_SEED, make_system
+    from las_inputs import WORKLOADS, make_system
     from oracle import las_oracle as O
     w = WORKLOAD
-    s = make_system(w["nao"], w["naux"], w["ncore"], w["frags"], seed=BASE_SEED + 2,
-                    with_B=False)
+    seed = WORKLOADS["nao1200"]["seed"]
+    s = make_system(w["nao"], w["naux"], w["ncore"], w["frags"], seed=seed, with_B=False)
     # the first sample_rows rows of the full-size B (same seed and counter layout)
-    Bs = _first_rows_B(BASE_SEED + 2, w["nao"], w["naux"], sample_rows)
+    Bs = _first_rows_B(seed, w["nao"], w["naux"], sample_rows)
     t0 = time.perf_counter()
     O.energy_grad(Bs, s.nao, s.h, s.C, s.ncore, s.dm1s, s.dm2, with_grad=True)
     dt = time.perf_counter() - t0

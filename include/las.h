@@ -49,7 +49,7 @@ typedef enum {
   LAS_ERR_WORKSPACE = 3,  /* workspace cap too small for the smallest chunk */
   LAS_ERR_TIMEOUT = 4,    /* a bounded device-side wait ran out */
   LAS_ERR_INTERNAL = 5,   /* a device-side consistency check failed */
-  LAS_ERR_UNSUPPORTED = 6 /* valid request this build does not support (e.g. sizes too large) */
+  LAS_ERR_UNSUPPORTED = 6 /* valid request the library does not support (e.g. sizes too large) */
 } las_status;
 
 typedef enum {

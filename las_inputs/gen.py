@@ -206,19 +206,20 @@ def make_system(nao: int, naux: int, ncore: int, frags: list[tuple[int, int]], s
     return sysm
 
 
-# Workloads (sizes as in the benchmark table of the design notes).
-CONFIGS = {
-    0: dict(nao=48, naux=160, ncore=10, frags=[(2, 2), (2, 2)]),
-    1: dict(nao=400, naux=1600, ncore=60, frags=[(4, 4)] * 4),
-    2: dict(nao=1200, naux=4800, ncore=150, frags=[(6, 8)] + [(4, 8)] * 4),
-    4: dict(nao=800, naux=3200, ncore=100, frags=[(6, 6)] * 4),
+# Workloads, named by their number of AOs, each with its own seed.
+WORKLOADS = {
+    "nao48": dict(nao=48, naux=160, ncore=10, frags=[(2, 2), (2, 2)], seed=BASE_SEED),
+    "nao400": dict(nao=400, naux=1600, ncore=60, frags=[(4, 4)] * 4, seed=BASE_SEED + 1),
+    "nao1200": dict(nao=1200, naux=4800, ncore=150, frags=[(6, 8)] + [(4, 8)] * 4,
+                    seed=BASE_SEED + 2),
+    "nao800": dict(nao=800, naux=3200, ncore=100, frags=[(6, 6)] * 4, seed=BASE_SEED + 4),
 }
 
 
-def config_system(idx: int, with_B: bool = True, threads: int | None = None) -> LasSystem:
-    cfg = CONFIGS[idx]
-    return make_system(cfg["nao"], cfg["naux"], cfg["ncore"], cfg["frags"],
-                       seed=BASE_SEED + idx, with_B=with_B, threads=threads)
+def workload_system(name: str, with_B: bool = True, threads: int | None = None) -> LasSystem:
+    w = WORKLOADS[name]
+    return make_system(w["nao"], w["naux"], w["ncore"], w["frags"], seed=w["seed"],
+                       with_B=with_B, threads=threads)
 
 
 def batched_specs(count: int = 64, seed: int = BASE_SEED + 3) -> list[dict]:

@@ -4,7 +4,7 @@ import functools
 import numpy as np
 import pytest
 
-from las_inputs import config_system, make_system
+from las_inputs import workload_system, make_system
 
 
 def torch_cuda():
@@ -44,7 +44,7 @@ def gpu_energy_grad(s, precision="fp64", want_gorb=True, **kw):
 
 
 SMALL = {
-    "cfg0": lambda: config_system(0),
+    "nao48": lambda: workload_system("nao48"),
     # sizes that are multiples of no tile, three uneven fragments, one odd-electron fragment
     "ragged": lambda: make_system(37, 53, 5, [(2, 3), (3, 2), (4, 4)], seed=4242),
     "nofrag": lambda: make_system(29, 45, 6, [], seed=99),

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from gpu_common import built, dev, torch_cuda
-from las_inputs import config_system
+from las_inputs import workload_system
 from oracle import las_oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -17,7 +17,7 @@ EPS = 1e-5
 def sys4():
     torch_cuda()
     built()
-    s = config_system(4)
+    s = workload_system("nao800")
     ref = O.system_energy_grad(s)
     return s, ref
 

@@ -19,7 +19,7 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable():
     assert selftest_bounded_wait() == LAS_ERR_TIMEOUT
     torch.cuda.synchronize()
     # the context and the device keep working afterwards
-    s = SMALL["cfg0"]()
+    s = SMALL["nao48"]()
     ref = O.system_energy_grad(s)
     for precision in ("fp64", "split"):
         E, G, _ = gpu_energy_grad(s, precision, want_gorb=False)

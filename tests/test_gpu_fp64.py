@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 from gpu_common import SMALL, built, dev, gpu_energy_grad, make_las, torch_cuda
-from las_inputs import config_system
+from las_inputs import workload_system
 from oracle import las_oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -49,7 +49,7 @@ def test_chunked_workspace_same_result():
 
 def test_workspace_cap_too_small_is_reported():
     from paper_2505_03755_gb300 import LasError
-    s = SMALL["cfg0"]()
+    s = SMALL["nao48"]()
     with pytest.raises(LasError) as ei:
         make_las(s, max_workspace_bytes=1000)
     assert ei.value.code == 3  # LAS_ERR_WORKSPACE
@@ -57,7 +57,7 @@ def test_workspace_cap_too_small_is_reported():
 
 def test_invalid_arguments():
     from paper_2505_03755_gb300 import LasDF, LasError
-    s = SMALL["cfg0"]()
+    s = SMALL["nao48"]()
     with pytest.raises(LasError) as ei:
         LasDF(dev(s.Bp), s.nao, s.naux, s.nmo, s.nao, s.nact)   # ncore + a > nmo
     assert ei.value.code == 1
@@ -130,7 +130,7 @@ def test_df_transform_matches_oracle():
 def test_autograd_backward_is_dEdC():
     torch = torch_cuda()
     from paper_2505_03755_gb300 import las_energy
-    s = SMALL["cfg0"]()
+    s = SMALL["nao48"]()
     las = make_las(s)
     C = dev(s.C).requires_grad_(True)
     E = las_energy(C, las, dev(s.h), dev(s.dm1s_flat()), dev(s.dm2_flat()))
@@ -140,8 +140,8 @@ def test_autograd_backward_is_dEdC():
     las.close()
 
 
-def test_config1_energy_grad():
-    s = config_system(1)
+def test_nao400_energy_grad():
+    s = workload_system("nao400")
     ref = O.system_energy_grad(s)
     E, G, g = gpu_energy_grad(s, "fp64")
     assert abs(E - ref["E"]) <= E_REL * abs(ref["E"])

@@ -1,10 +1,10 @@
 """Orbital Hessian-vector product (las_orbital_hvp) against the oracle's analytic linearisation
-of the gradient, in both precisions, on small ragged systems and config1 (Nao=400)."""
+of the gradient, in both precisions, on small ragged systems and the Nao=400 workload."""
 import numpy as np
 import pytest
 
 from gpu_common import SMALL, built, dev, torch_cuda
-from las_inputs import config_system
+from las_inputs import workload_system
 from oracle import las_oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -33,11 +33,11 @@ def _check(s, precision, tol, seed):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("split", 1e-9)])
-@pytest.mark.parametrize("name", ["cfg0", "ragged", "nofrag", "nmo_lt_nao"])
+@pytest.mark.parametrize("name", ["nao48", "ragged", "nofrag", "nmo_lt_nao"])
 def test_orbital_hvp_small(precision, tol, name):
     _check(SMALL[name](), precision, tol, seed=21)
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("split", 1e-9)])
-def test_orbital_hvp_config1(precision, tol):
-    _check(config_system(1), precision, tol, seed=22)
+def test_orbital_hvp_nao400(precision, tol):
+    _check(workload_system("nao400"), precision, tol, seed=22)

@@ -10,12 +10,12 @@ in seconds, so two properties that hold at any size stand in for it:
   bound (the halves' digit exponents differ from the whole's).
 
 The oracle itself pins the same system over its first and last auxiliary rows in
-test_gpu_config2_slices.py."""
+test_gpu_nao1200_slices.py."""
 import numpy as np
 import pytest
 
 from gpu_common import built, dev, torch_cuda
-from las_inputs import config_system
+from las_inputs import workload_system
 
 pytestmark = pytest.mark.gpu
 
@@ -25,7 +25,7 @@ def full():
     torch = torch_cuda()
     built()
     torch.cuda.empty_cache()
-    s = config_system(2)
+    s = workload_system("nao1200")
     B = dev(s.Bp)
     s.Bp = None   # the host copy (27.7 GB) is no longer needed
     yield s, B
@@ -44,7 +44,7 @@ def _eval(s, B, naux, precision, C, h, dm1s, dm2):
         las.close()
 
 
-def test_config2_full_size(full):
+def test_nao1200_full_size(full):
     import torch
     s, B = full
     assert B.numel() > 2**31

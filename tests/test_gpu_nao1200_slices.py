@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from gpu_common import built, dev, torch_cuda
-from las_inputs import BASE_SEED, CONFIGS, make_system, packed_B_rows
+from las_inputs import WORKLOADS, make_system, packed_B_rows
 from oracle import las_oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -16,12 +16,11 @@ ROWS = 120
 
 @pytest.fixture(scope="module")
 def workload():
-    c = CONFIGS[2]
-    s = make_system(c["nao"], c["naux"], c["ncore"], c["frags"], seed=BASE_SEED + 2,
-                    with_B=False)
+    c = WORKLOADS["nao1200"]
+    s = make_system(c["nao"], c["naux"], c["ncore"], c["frags"], seed=c["seed"], with_B=False)
     slices = {}
     for l0 in (0, c["naux"] - ROWS):
-        Bs = packed_B_rows(BASE_SEED + 2, c["nao"], c["naux"], l0, l0 + ROWS)
+        Bs = packed_B_rows(c["seed"], c["nao"], c["naux"], l0, l0 + ROWS)
         ref = O.energy_grad(Bs, s.nao, s.h, s.C, s.ncore, s.dm1s, s.dm2, with_grad=True)
         slices[l0] = (Bs, ref)
     return s, slices
@@ -29,7 +28,7 @@ def workload():
 
 @pytest.mark.parametrize("precision", ["fp64", "split"])
 @pytest.mark.parametrize("which", ["first", "last"])
-def test_config2_slice(workload, precision, which):
+def test_nao1200_slice(workload, precision, which):
     torch_cuda()
     built()
     from paper_2505_03755_gb300 import LasDF

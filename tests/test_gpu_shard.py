@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from gpu_common import SMALL, built, dev, gpu_energy_grad, torch_cuda
-from las_inputs import config_system
+from las_inputs import workload_system
 from oracle import las_oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -37,7 +37,7 @@ def _sharded(s, precision, world):
 
 
 @pytest.mark.parametrize("precision,world", [("fp64", 2), ("fp64", 3), ("split", 3)])
-@pytest.mark.parametrize("name", ["ragged", "cfg0"])
+@pytest.mark.parametrize("name", ["ragged", "nao48"])
 def test_shards_add_up_small(name, precision, world):
     s = SMALL[name]()
     ref = O.system_energy_grad(s)
@@ -59,15 +59,15 @@ def test_shards_add_up_small(name, precision, world):
 
 
 @functools.lru_cache(maxsize=None)
-def _config1():
-    s = config_system(1)
+def _nao400():
+    s = workload_system("nao400")
     return s, O.system_energy_grad(s)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "split"])
-def test_shards_add_up_config1(precision):
+def test_shards_add_up_nao400(precision):
     """Nao=400, Naux=1600 in three blocks (534, 533, 533 rows: ragged against every tile)."""
-    s, ref = _config1()
+    s, ref = _nao400()
     E, G, g = _sharded(s, precision, 3)
     if precision == "fp64":
         assert abs(E - ref["E"]) <= 1e-10 * abs(ref["E"])

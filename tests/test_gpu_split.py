@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 from gpu_common import SMALL, built, dev, gpu_energy_grad, make_las, torch_cuda
-from las_inputs import config_system
+from las_inputs import workload_system
 from oracle import las_oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -95,7 +95,7 @@ def test_split_chunked_workspace_same_result():
 
 def test_split_autograd():
     from paper_2505_03755_gb300 import las_energy
-    s = SMALL["cfg0"]()
+    s = SMALL["nao48"]()
     las = make_las(s, "split")
     C = dev(s.C).requires_grad_(True)
     E = las_energy(C, las, dev(s.h), dev(s.dm1s_flat()), dev(s.dm2_flat()))
@@ -105,15 +105,15 @@ def test_split_autograd():
     las.close()
 
 
-def test_config1_split():
-    s = config_system(1)
+def test_nao400_split():
+    s = workload_system("nao400")
     ref = O.system_energy_grad(s)
     E, G, _ = gpu_energy_grad(s, "split", want_gorb=False)
     assert abs(E - ref["E"]) <= E_ABS
     assert np.abs(G - ref["G"]).max() <= G_ABS
 
 
-@pytest.mark.parametrize("name", ["ragged", "cfg0"])
+@pytest.mark.parametrize("name", ["ragged", "nao48"])
 def test_split_df_jk(name):
     s = SMALL[name]()
     las = make_las(s, "split")
@@ -125,7 +125,7 @@ def test_split_df_jk(name):
     las.close()
 
 
-@pytest.mark.parametrize("name,p0,p1", [("ragged", 3, 30), ("cfg0", 0, 48), ("nmo_lt_nao", 5, 30)])
+@pytest.mark.parametrize("name,p0,p1", [("ragged", 3, 30), ("nao48", 0, 48), ("nmo_lt_nao", 5, 30)])
 def test_split_df_transform(name, p0, p1):
     """(L|mu u) and (L|pu) (Eqs. ao2mo_1, ao2mo_2) in split precision, p over a ragged range."""
     s = SMALL[name]()
@@ -139,9 +139,9 @@ def test_split_df_transform(name, p0, p1):
     las.close()
 
 
-def test_split_df_transform_chunked_config1():
-    """config1 (Nao=400) with a workspace cap that splits the auxiliary index into chunks."""
-    s = config_system(1)
+def test_split_df_transform_chunked_nao400():
+    """The Nao=400 workload with a workspace cap that splits the auxiliary index into chunks."""
+    s = workload_system("nao400")
     las = make_las(s, "split", max_workspace_bytes=256 << 20)
     a0, a1 = s.ncore, s.ncore + s.nactive
     lmu, lpu = las.df_transform(dev(s.C), 0, s.nmo)

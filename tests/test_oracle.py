@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 import scipy.linalg as sl
 
-from las_inputs import config_system, make_system, splitmix64
+from las_inputs import workload_system, make_system, splitmix64
 from las_inputs.rdm import fragment_rdms, nstrings, strings
 from oracle import las_oracle as O
 
@@ -19,8 +19,8 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 @pytest.fixture(scope="module")
-def cfg0():
-    return config_system(0)
+def nao48():
+    return workload_system("nao48")
 
 
 @pytest.fixture(scope="module")
@@ -38,8 +38,8 @@ def test_splitmix64_golden():
         assert got == int(ref, 16)
 
 
-def test_generator_properties(cfg0):
-    s = cfg0
+def test_generator_properties(nao48):
+    s = nao48
     assert np.abs(s.C.T @ s.C - np.eye(s.nmo)).max() < 1e-13
     assert np.allclose(s.h, s.h.T)
     # B decays along L as exp(-L/Naux): compare mean squares of first and last quarters
@@ -101,8 +101,8 @@ def test_df_jk_brute_force():
         assert np.abs(eri - eri.transpose(perm)).max() < 1e-13
 
 
-def test_active_integral_symmetry(cfg0):
-    s = cfg0
+def test_active_integral_symmetry(nao48):
+    s = nao48
     a = s.nactive
     C_a = s.C[:, s.ncore:s.ncore + a]
     eri, mveri = O.ao2mo_active(s.Bp, s.nao, C_a)
@@ -116,8 +116,8 @@ def test_active_integral_symmetry(cfg0):
     assert np.abs(full - eri).max() < 1e-12
 
 
-def test_df_transform_matches_mo_integrals(cfg0):
-    s = cfg0
+def test_df_transform_matches_mo_integrals(nao48):
+    s = nao48
     a0, a1 = s.ncore, s.ncore + s.nactive
     lmu, lpu = O.df_transform(s.Bp, s.nao, s.C, (a0, a1), 0, s.nmo)
     b = O.unpack_block(s.Bp, s.nao)
@@ -246,8 +246,8 @@ def test_grad_derivative_symmetric_and_exact_on_the_energy(small3):
     assert abs(d2 - np.sum(dC1 * r1["dG"])) <= 1e-7 * abs(d2)
 
 
-def test_grad_derivative_finite_differences(cfg0):
-    s = cfg0
+def test_grad_derivative_finite_differences(nao48):
+    s = nao48
     dC = np.random.default_rng(12).standard_normal(s.C.shape)
     r = O.grad_derivative(s.Bp, s.nao, s.h, s.C, s.ncore, s.dm1s, s.dm2, dC)
     eps = 1e-4
@@ -268,7 +268,7 @@ def test_orbital_hvp_finite_differences(small3):
         assert np.abs(r["Dg"] + r["Dg"].T).max() <= 1e-12 * np.abs(r["Dg"]).max()
 
 
-@pytest.mark.parametrize("which", ["cfg0", "small3"])
+@pytest.mark.parametrize("which", ["nao48", "small3"])
 def test_energy_three_ways(which, request):
     s = request.getfixturevalue(which)
     eb = O.system_energy_grad(s, with_grad=False)["E"]
@@ -320,8 +320,8 @@ def test_no_fragments_rhf():
     assert np.abs(r["G"][:, 4:]).max() == 0.0
 
 
-def test_rotation_invariances(cfg0):
-    s = cfg0
+def test_rotation_invariances(nao48):
+    s = nao48
     base = O.system_energy_grad(s)
     rng = np.random.default_rng(3)
     c = s.ncore
@@ -346,8 +346,8 @@ def test_rotation_invariances(cfg0):
     assert np.abs(g + g.T).max() == 0.0
 
 
-def test_positivity(cfg0):
-    s = cfg0
+def test_positivity(nao48):
+    s = nao48
     r = O.system_energy_grad(s, with_grad=False)
     Dc = 2 * s.C[:, :s.ncore] @ s.C[:, :s.ncore].T
     assert np.sum(Dc * r["J"]) >= 0
@@ -374,17 +374,17 @@ def _fd_check(s, ndir, eps=1e-4, seed=0):
     return worst
 
 
-def test_finite_differences(cfg0):
-    assert _fd_check(cfg0, 20) < 1e-6
+def test_finite_differences(nao48):
+    assert _fd_check(nao48, 20) < 1e-6
 
 
 def test_finite_differences_odd_fragment(small3):
     assert _fd_check(small3, 6) < 1e-6
 
 
-def test_planted_mistakes(cfg0, monkeypatch):
+def test_planted_mistakes(nao48, monkeypatch):
     """Each planted slip in the oracle must be caught by one of the pins above."""
-    s = cfg0
+    s = nao48
     good = O.system_energy_grad(s, with_grad=False)["E"]
     esc = O.energy_slater_condon(s)
     assert abs(good - esc) < 1e-10
