@@ -56,3 +56,24 @@ def test_binding_shape_checks():
         _shape_check(torch.zeros(7, dtype=torch.float64), 8, "dm2")
     with pytest.raises(ValueError):
         _shape_check(torch.zeros(12, dtype=torch.float64), (4, 3), "C")       # flat for a matrix
+
+
+def test_header_is_c99_and_a_c_client_links(tmp_path):
+    """include/las.h compiles as strict C99 and a C program linked against liblasdf.so gets
+    the documented argument errors from the calls that check before any device work."""
+    import shutil
+    import subprocess
+    import pytest
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    import __graft_entry__ as g
+    g.build()
+    pkg = os.path.join(ROOT, "paper_2505_03755_gb300")
+    exe = str(tmp_path / "abi_from_c")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "abi_from_c.c"),
+                    "-L", pkg, "-llasdf", "-Wl,-rpath," + pkg, "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "ok"
