@@ -223,7 +223,8 @@ int las_stage_times(las_ctx* ctx, float* ms, int cap);
  *   C[M][N] = A[M][K] * B[K][N]   (row-major, leading dimensions lda >= K, ldb >= N, ldc >= N)
  * A is scaled per row and B per column by powers of two, each cut into six BF16 digits, and the
  * 21 digit products of total weight <= 2^-40 are formed with exact FP32 partial sums for the
- * three leading weights (integer recombination) and one FP32 sum for the rest.  The error is
+ * four leading weights 2^0 ... 2^-24 (flushed to integers and recombined in integer arithmetic)
+ * and one FP32 sum for the weights 2^-32 and 2^-40.  The error is
  * that of truncating both operands to 47 bits below their row / column maximum.
  * The method has no counterpart in the paper (which runs FP64 GEMMs and names reduced precision
  * only as an outlook, section "Outlook"); it implements that outlook for this hardware.
