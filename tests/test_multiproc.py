@@ -118,3 +118,4 @@ def test_two_rank_aux_sharded_energy_grad_equals_whole_system():
     # a share on its own is not the answer (the partition is real)
     half = O.energy_grad(s.Bp, s.nao, s.h, s.C, s.ncore, s.dm1s, s.dm2, l0=0, l1=27)
     assert abs(half["E"] - ref["E"]) > 1e-6 * abs(ref["E"])
+
