@@ -77,3 +77,22 @@ def test_header_is_c99_and_a_c_client_links(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == "ok"
+
+
+def test_no_cpu_fallback(monkeypatch, tmp_path):
+    """Without the compiled library, or with host tensors, the product path raises instead of
+    computing anything on the CPU."""
+    import types
+    import pytest
+    import torch
+    from paper_2505_03755_gb300 import las
+    monkeypatch.setattr(las, "_lib", None)
+    with pytest.raises(RuntimeError, match="not found"):
+        las.load_library(str(tmp_path / "liblasdf.so"))
+    monkeypatch.undo()
+    import __graft_entry__ as g
+    g.build()
+    n, X = 6, 4
+    B = torch.zeros(X * n * (n + 1) // 2, dtype=torch.float64)          # a host tensor
+    with pytest.raises(TypeError, match="CUDA"):
+        las.LasDF(B, n, X, n, 2, [], stream=types.SimpleNamespace(cuda_stream=0))
