@@ -498,3 +498,28 @@ def test_planted_dropped_ragged_block(many_blocks, monkeypatch):
 
     monkeypatch.setattr(O, "p_blocks", bad_blocks)
     assert abs(O.system_energy_grad(s, with_grad=False)["E"] - ea) > 1e-6 * abs(ea)
+
+
+SWEEP = [
+    # (nao, naux, ncore, fragments (nelec, norb), nmo, seed)
+    (9, 27, 0, [(2, 3)], None, 101),                     # no core, one open fragment
+    (10, 33, 4, [(1, 2), (3, 3)], None, 102),            # two odd-electron fragments
+    (12, 41, 1, [(2, 2), (2, 2), (2, 2)], 10, 103),      # three fragments, nmo < nao
+    (11, 250, 3, [(4, 3)], None, 104),                   # fragment with a hole pair; 2 blocks
+    (13, 29, 2, [(0, 2), (4, 4)], 12, 105),              # an empty fragment (no electrons)
+    (8, 20, 3, [], None, 106),                           # closed shell only
+]
+
+
+@pytest.mark.parametrize("nao,naux,ncore,frags,nmo,seed", SWEEP)
+def test_energy_three_ways_sweep(nao, naux, ncore, frags, nmo, seed):
+    """Tier B (J/K form), Tier A (explicit MO integrals, full-molecule RDMs) and Slater-Condon
+    over the explicit product CI vector agree on systems of varied shape, and the analytic
+    gradient matches central differences there."""
+    s = make_system(nao, naux, ncore, frags, seed=seed, nmo=nmo)
+    eb = O.system_energy_grad(s, with_grad=False)["E"]
+    ea = O.energy_tier_a(s.Bp, s.nao, s.h, s.C, s.ncore, s.dm1s, s.dm2)
+    esc = O.energy_slater_condon(s)
+    assert abs(ea - eb) < 1e-12 * max(1.0, abs(eb))
+    assert abs(esc - eb) < 1e-12 * max(1.0, abs(eb))
+    assert _fd_check(s, 3, seed=seed) < 1e-6
