@@ -236,19 +236,22 @@ las_status las_split_gemm(long M, long N, long K, const double* A, long lda, con
                           size_t workspace_bytes, void* stream);
 
 /* Allocation-free emulated-FP64 GEMM: the same product as las_split_gemm for callers that
- * cannot allocate device memory where they need it -- code running while a stream is being
- * captured into a CUDA graph, plugins whose host application owns every device allocation, or
- * loops where a cudaMalloc could synchronise the device.  The paper has no counterpart; this is
- * a service of this library.
+ * cannot allocate device memory where they need a product -- plugins whose host application
+ * owns every device allocation through its own pool (a cudaMalloc behind its back would break
+ * its accounting or fail), or loops where a cudaMalloc could synchronise the device.  The paper
+ * has no counterpart; this is a service of this library.
  * Scratch: a fixed LAS_NOALLOC_SCRATCH_BYTES device array inside the library image (held by
  * every GPU that loads the library until the process exits); nothing is allocated or freed.
  * Sizes whose digit planes do not fit the array, i.e. las_split_gemm_workspace(M, N, K) >
  * LAS_NOALLOC_SCRATCH_BYTES, are rejected with LAS_ERR_WORKSPACE before any GPU work.
  * The first call on each device looks up the array's device address (with that device
- * current); make that first call before any stream capture begins.
- * All calls share the one array: calls that may overlap on the GPU (different streams or host
- * threads without ordering) race and must be serialised by the caller.
- * Synchronous, like las_split_gemm. */
+ * current) and keeps it for later calls; make that first call before any stream capture
+ * begins.  A reset of the device's primary context (cudaDeviceReset) invalidates the kept
+ * address: do not call this entry point after such a reset.
+ * All calls share the one array, which keeps the last call's contents: calls that may overlap
+ * on the GPU (different streams or host threads without ordering) race and must be serialised
+ * by the caller.
+ * Synchronous, like las_split_gemm: it waits for its stream and reads a status word back. */
 #define LAS_NOALLOC_SCRATCH_BYTES (64u << 20)
 las_status las_split_gemm_noalloc(long M, long N, long K, const double* A, long lda,
                                   const double* B, long ldb, double* C, long ldc, void* stream);

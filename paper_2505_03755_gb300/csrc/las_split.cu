@@ -1449,14 +1449,14 @@ extern "C" las_status las_selftest_bounded_wait(void* stream) {
 // ------------------------------------------------------------------------------------------
 // Allocation-free variant of las_split_gemm
 //
-// Some callers cannot allocate device memory at the point where they need a product: code that
-// runs while a stream is being captured into a CUDA graph (cudaMalloc is not a graph operation),
-// plugins whose host application owns every device allocation through its own pool, and
+// Some callers cannot allocate device memory at the point where they need a product: plugins
+// whose host application owns every device allocation through its own pool, and
 // latency-critical loops where a cudaMalloc could synchronise the device. This entry point takes
 // its scratch from a fixed array that is part of the library image instead of asking for a
 // buffer: the digit planes and exponents of both operands live in `g_noalloc_scratch`, a
 // LAS_NOALLOC_SCRATCH_BYTES (64 MiB) file-scope device array that every GPU which loads the
-// library holds until the process exits.
+// library holds until the process exits.  Like las_split_gemm it waits for its stream and reads
+// its status word back before returning.
 // ------------------------------------------------------------------------------------------
 #include <mutex>
 

@@ -439,6 +439,11 @@ def split_gemm(A, B, out=None, stream=None):
         raise ValueError("inner dimensions differ")
     C = torch.empty((M, N), dtype=torch.float64, device=A.device) if out is None else out
     _shape_check(C, (M, N), "out")
+    # the library builds its tensor maps and launches on the current device
+    cur = torch.device("cuda", torch.cuda.current_device())
+    for t, name in ((A, "A"), (B, "B"), (C, "out")):
+        if t.device != cur:
+            raise ValueError(f"{name}: on {t.device}, the current CUDA device is {cur}")
     nbytes = int(lib.las_split_gemm_workspace(M, N, K))
     ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=A.device)
     st = (stream or torch.cuda.current_stream()).cuda_stream

@@ -10,7 +10,7 @@ def test_reference_arm_json_line():
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "3", "--cpu-rows", "8"],
+                        "--steps", "1", "--warmup", "3", "--ref-rows", "8"],
                        capture_output=True, text=True, timeout=600, cwd=root)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
@@ -25,3 +25,6 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["workload"].startswith("nao1200")
+    # the step is a bounded sample of one evaluation: the line says so and its step time is
+    # the measured one
+    assert "value_projection" in d and d["ms_per_step"] < 60e3

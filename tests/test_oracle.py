@@ -50,6 +50,43 @@ def test_generator_properties(nao48):
     assert abs(r / expect - 1) < 0.1
 
 
+def test_unpack_block_packed_index_convention():
+    """The packed layout of the Cholesky vectors (lower triangle per auxiliary index, section
+    "Calculation of effective potentials"): element mu(mu+1)/2 + nu, mu >= nu, is b_{mu nu} and,
+    by symmetry, b_{nu mu}.  Written out by hand for n = 3 so that a row-order slip (the upper
+    triangle's order, or nu(nu+1)/2 + mu) cannot hide behind numpy's index helpers."""
+    row = np.array([[10.0, 21.0, 22.0, 31.0, 32.0, 33.0]])   # b00 b10 b11 b20 b21 b22
+    expect = np.array([[10.0, 21.0, 31.0],
+                       [21.0, 22.0, 32.0],
+                       [31.0, 32.0, 33.0]])
+    assert np.array_equal(O.unpack_block(row, 3)[0], expect)
+    # n = 4, one auxiliary row per element: only (mu, nu) and (nu, mu) are hit
+    n = 4
+    P = n * (n + 1) // 2
+    for mu in range(n):
+        for nu in range(mu + 1):
+            one = np.zeros((1, P))
+            one[0, mu * (mu + 1) // 2 + nu] = 1.0
+            sq = O.unpack_block(one, n)[0]
+            hit = np.zeros((n, n))
+            hit[mu, nu] = hit[nu, mu] = 1.0
+            assert np.array_equal(sq, hit), (mu, nu)
+
+
+def test_unpacked_generator_band(nao48):
+    """Unpacked, the seeded Cholesky vectors show the band of the generator recipe,
+    rms of b_{mu nu} over (L, mu) falling as exp(-|mu - nu|/8): a packed-index slip in the
+    oracle's unpacking would scramble the band."""
+    s = nao48
+    b = O.unpack_block(s.Bp, s.nao)
+    w = np.exp(-np.arange(s.naux) / s.naux)
+    b = b / w[:, None, None]                        # remove the decay along L
+    rms = [np.sqrt(np.mean(np.diagonal(b, offset=d, axis1=1, axis2=2) ** 2))
+           for d in range(0, 25)]
+    for d in range(25):
+        assert abs(rms[d] / rms[0] - math.exp(-d / 8.0)) < 0.08 * math.exp(-d / 8.0), d
+
+
 def test_rdm_sum_rules():
     for ne, m in [(2, 2), (4, 4), (6, 8), (3, 3), (6, 6)]:
         from las_inputs.gen import ci_vector
@@ -440,6 +477,24 @@ def test_planted_mistakes(nao48, monkeypatch):
     monkeypatch.setattr(O, "energy_grad", bad_grad)
     assert _fd_check(s, 3) > 1e-3
     monkeypatch.setattr(O, "energy_grad", orig_eg)
+
+    # (5) the packed triangle unpacked in the upper triangle's row order: both unpacking pins
+    # must fail (every energy route unpacks through the same function, so they cannot see it)
+    orig_up = O.unpack_block
+
+    def bad_unpack(Bp_rows, n):
+        out = np.zeros((Bp_rows.shape[0], n, n))
+        mu, nu = np.triu_indices(n)
+        out[:, mu, nu] = Bp_rows
+        out[:, nu, mu] = Bp_rows
+        return out
+
+    monkeypatch.setattr(O, "unpack_block", bad_unpack)
+    with pytest.raises(AssertionError):
+        test_unpack_block_packed_index_convention()
+    with pytest.raises(AssertionError):
+        test_unpacked_generator_band(s)
+    monkeypatch.setattr(O, "unpack_block", orig_up)
 
 
 @pytest.fixture(scope="module")

@@ -1,5 +1,6 @@
 """The allocation-free GEMM entry point (for callers that cannot allocate device memory where
-they need a product, e.g. inside CUDA-graph capture or under a host-owned memory pool).
+they need a product: host applications that own every device allocation through their own pool,
+or loops where a cudaMalloc could synchronise the device).
 
 It must give the same product as the allocating entry point, twice in a row (the shared scratch
 array keeps the previous call's contents), and must refuse sizes beyond its fixed scratch.
