@@ -41,7 +41,6 @@ def workload_config(ws: int = 1) -> dict:
 
 
 METRIC = "LAS energy+gradient evals/s at Nao=1200 (FP64 vs split-prec), % of roofline"
-FP64_NOMINAL_TFLOPS = 1.25      # nominal FP64 (DFMA/DMMA) rate of GB300
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -198,6 +197,13 @@ def run_ours(args, ws, rank, local):
 
     precs = ["split", "fp64"] if args.precision == "both" else [args.precision]
     results = {}
+    # the FP64 roofline's denominator, measured on this GPU in this run (register-resident
+    # DMMA and DFMA loops over all SMs)
+    fp64_peak = None
+    if "fp64" in precs:
+        from paper_2505_03755_gb300 import probe_fp64
+        dmma, dfma = probe_fp64()
+        fp64_peak = {"dmma_tflops": dmma, "dfma_tflops": dfma}
     for prec in precs:
         steps = args.steps if prec == precs[0] else max(1, min(args.steps, args.fp64_steps))
         warm = args.warmup if prec == precs[0] else max(1, min(args.warmup, args.fp64_warmup))
@@ -309,7 +315,8 @@ def run_ours(args, ws, rank, local):
                              stage_ms=stage_ms, E=E_val,
                              e2e_evals_per_s=weak_scaling_rate(ws, steps, t_e2e), e2e_E=e2e_E,
                              h2d=bi, d2h=bo, clocks=ck, launches=launches, jk_ms=jk_ms,
-                             veff_ms=veff_ms, hvp_ms=hvp_ms, dft_ms=dft_ms)
+                             veff_ms=veff_ms, hvp_ms=hvp_ms, dft_ms=dft_ms,
+                             fp64_peak=fp64_peak if prec == "fp64" else None)
     del Bd
     torch.cuda.empty_cache()
     return s, work, peaks, results, tgen
@@ -340,11 +347,14 @@ def roofline_for(prec, r, work, peaks, s):
                 "algorithmic_flops": flops}
     if prec == "fp64":
         achieved = work["s1"] / t_s1 / 1e12
-        return {"bound": "tensor", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+        pk = r.get("fp64_peak") or {}
+        peak = pk.get("dmma_tflops")
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
                 "kernel": "k_gemm_f64 (half transform, DMMA)",
-                "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in "
-                               "MEASURED_PEAKS.json)"}
+                "peak_source": "measured in this run: las_probe_fp64 DMMA loop (mma.sync "
+                               "m16n8k4 f64, all SMs, register-resident), of measured",
+                "dfma_tflops_measured": pk.get("dfma_tflops")}
     return None
 
 
@@ -385,6 +395,127 @@ def run_ao2mo(local: int) -> dict:
         ms = e0.elapsed_time(e1) / calls
         las.close()
         out[prec] = {"ms": ms, "calls": calls, "fp64_equiv_tflops": flops / (ms / 1e3) / 1e12}
+    del Bd
+    torch.cuda.empty_cache()
+    return out
+
+
+def _guarded(fn, *a):
+    """A side measurement that fails reports its error in its own block of the line."""
+    try:
+        return fn(*a)
+    except Exception as e:  # noqa: BLE001 - any failure of a side block
+        import torch
+        torch.cuda.empty_cache()
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
+
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_nao400(local: int, reps: int = 20) -> dict:
+    """The mid-size workload (Nao=400, Naux=1600, Ncore=60, 4 x (4e,4o)): one energy+gradient
+    evaluation timed over `reps` repeats in both precisions (CUDA events on the library's
+    stream), and the oracle's evaluation of the same system timed once on the host cores."""
+    import torch
+    from las_inputs import workload_system
+    from oracle import las_oracle as O
+    from paper_2505_03755_gb300 import LasDF
+    dev = torch.device(f"cuda:{local}")
+    s = workload_system("nao400")
+    t0 = time.perf_counter()
+    ref = O.system_energy_grad(s)
+    t_oracle = time.perf_counter() - t0
+    Bd = torch.from_numpy(s.Bp).to(dev)
+    C, h = torch.from_numpy(s.C).to(dev), torch.from_numpy(s.h).to(dev)
+    d1, d2 = torch.from_numpy(s.dm1s_flat()).to(dev), torch.from_numpy(s.dm2_flat()).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    out = {"workload": "nao400_naux1600_core60_4x(4e,4o)", "repeats": reps,
+           "oracle": {"seconds": t_oracle, "evals_per_s": 1.0 / t_oracle,
+                      "cores": os.cpu_count(), "kind": "oracle (whole evaluation)"}}
+    for prec in ("split", "fp64"):
+        las = LasDF(Bd, s.nao, s.naux, s.nmo, s.ncore, s.nact, precision=prec, stream=stream)
+        E = torch.empty((), dtype=torch.float64, device=dev)
+        G = torch.empty((s.nao, s.nmo), dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                las.energy_grad(C, h, d1, d2, E=E, G=G)
+            las.sync()
+            e0, e1 = _events()
+            e0.record(stream)
+            for _ in range(reps):
+                las.energy_grad(C, h, d1, d2, E=E, G=G)
+            e1.record(stream)
+            e1.synchronize()
+        las.sync()
+        ms = e0.elapsed_time(e1) / reps
+        out[prec] = {"ms_per_eval": ms, "evals_per_s": 1e3 / ms,
+                     "abs_dE_vs_oracle_Eh": abs(float(E.item()) - ref["E"]),
+                     "max_abs_dG_vs_oracle": float(np.abs(G.cpu().numpy() - ref["G"]).max())}
+        las.close()
+    del Bd
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_nao800_fd(local: int, ndir: int = 200, eps: float = 1e-5) -> dict:
+    """The differentiation workload (Nao=800, Naux=3200, Ncore=100, 4 x (6e,6o), 40 GB
+    workspace cap): one forward + backward of the torch.autograd.Function in each precision,
+    and, in split precision, the central differences of the energy along `ndir` seeded
+    antisymmetric rotations (2 * ndir energy evaluations; the rotated coefficients are formed
+    on the device by torch outside the timed calls)."""
+    import torch
+    from las_inputs import workload_system
+    from paper_2505_03755_gb300 import LasDF, las_energy
+    dev = torch.device(f"cuda:{local}")
+    s = workload_system("nao800")
+    Bd = torch.from_numpy(s.Bp).to(dev)
+    s.Bp = None
+    h = torch.from_numpy(s.h).to(dev)
+    d1, d2 = torch.from_numpy(s.dm1s_flat()).to(dev), torch.from_numpy(s.dm2_flat()).to(dev)
+    C0 = torch.from_numpy(s.C).to(dev)
+    out = {"workload": "nao800_naux3200_core100_4x(6e,6o)", "workspace_cap_gb": 40}
+    stream = torch.cuda.current_stream(dev)
+    for prec in ("split", "fp64"):
+        las = LasDF(Bd, s.nao, s.naux, s.nmo, s.ncore, s.nact, precision=prec,
+                    max_workspace_bytes=40 << 30, stream=stream)
+        C = C0.clone().requires_grad_(True)
+        las_energy(C, las, h, d1, d2).backward()      # warm-up
+        C.grad = None
+        e0, e1 = _events()
+        e0.record(stream)
+        E = las_energy(C, las, h, d1, d2)
+        E.backward()
+        e1.record(stream)
+        e1.synchronize()
+        rec = {"autograd_fwd_bwd_ms": e0.elapsed_time(e1)}
+        if prec == "split":
+            G = C.grad.detach()
+            gen = torch.Generator(device="cpu").manual_seed(2024)
+            worst, ms = 0.0, 0.0
+            for _ in range(ndir):
+                X = torch.randn(s.nmo, s.nmo, generator=gen, dtype=torch.float64)
+                X = (X - X.T)
+                X = (X / torch.linalg.norm(X)).to(dev)
+                Cp = C0 @ torch.linalg.matrix_exp(eps * X)
+                Cm = C0 @ torch.linalg.matrix_exp(-eps * X)
+                a0, a1 = _events()
+                a0.record(stream)
+                Ep = las.energy(Cp, h, d1, d2)
+                Em = las.energy(Cm, h, d1, d2)
+                a1.record(stream)
+                a1.synchronize()
+                ms += a0.elapsed_time(a1)
+                fd = (float(Ep) - float(Em)) / (2 * eps)
+                an = float(torch.sum((C0.T @ G) * X))
+                worst = max(worst, abs(fd - an) / max(1.0, abs(an)))
+            rec.update({"fd_directions": ndir, "fd_energy_evals": 2 * ndir,
+                        "fd_gpu_ms_total": ms, "fd_energy_evals_per_s": 2 * ndir / (ms / 1e3),
+                        "fd_worst_rel_err": worst})
+        out[prec] = rec
+        las.close()
     del Bd
     torch.cuda.empty_cache()
     return out
@@ -513,7 +644,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="both", choices=["both", "split", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--fp64-warmup", type=int, default=3)
     ap.add_argument("--cpu-rows", type=int, default=240,
                     help="auxiliary rows of the oracle's bounded sample (cpu_baseline)")
@@ -524,6 +655,8 @@ def main():
                     help="skip the fragment-embedding AO2MO measurement")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-system batched (captured graph) measurement")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the Nao=400 and Nao=800 (differentiation) blocks")
     ap.add_argument("--profile-naux", type=int, default=None, metavar="N",
                     help="profiling only: the same system with its first N auxiliary functions "
                          "(a few GB on the device, for ncu captures); not a bench line")
@@ -537,6 +670,7 @@ def main():
         args.no_cpu_baseline = True
         args.no_ao2mo = True
         args.no_batched = True
+        args.no_other_workloads = True
     if args.split_gemm:
         split_gemm_probe(args.split_gemm, args.steps, args.warmup)
         return
@@ -589,6 +723,9 @@ def main():
         else None
     batched = run_batched(local) if (ws == 1 and not args.no_batched and
                                      args.precision == "both") else None
+    others = ws == 1 and not args.no_other_workloads and args.precision == "both"
+    nao400 = _guarded(run_nao400, local) if others else None
+    nao800 = _guarded(run_nao800_fd, local) if others else None
     # split against FP64 on the same inputs (the oracle cannot evaluate this size in seconds;
     # its parity at this size is tested on auxiliary slices)
     accuracy = None
@@ -630,6 +767,7 @@ def main():
                     "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
             "gpu_launches": r["launches"], "clocks": r["clocks"], "modes": modes,
             "split_vs_fp64": accuracy, "frag_ao2mo": ao2mo, "batched": batched,
+            "nao400": nao400, "nao800_differentiation": nao800,
             "input_generation_s": tgen}
     print(json.dumps(line), flush=True)
     if ws > 1:

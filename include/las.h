@@ -262,6 +262,14 @@ las_status las_split_gemm_noalloc(long M, long N, long K, const double* A, long 
  * LAS_ERR_CUDA on a CUDA error.  stream: cudaStream_t or NULL. */
 las_status las_selftest_bounded_wait(void* stream);
 
+/* FP64 throughput probe (no counterpart in the paper; the denominator of the native-FP64
+ * roofline): two register-resident loops over all SMs of the current device, one of FP64
+ * tensor-core MMAs (mma.sync m16n8k4 f64, the instruction of the FP64 GEMMs) and one of FP64
+ * fused multiply-adds, each timed with CUDA events on `stream` after a warm-up launch.
+ * dmma_tflops, dfma_tflops: host pointers, written with the measured rates in TFLOP/s.
+ * Allocates and frees 8 bytes of device memory.  Synchronous (about a second). */
+las_status las_probe_fp64(double* dmma_tflops, double* dfma_tflops, void* stream);
+
 /* Number of kernels this library has launched in this process so far (all contexts). */
 long las_kernel_launches(void);
 

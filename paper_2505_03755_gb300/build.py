@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblasdf.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["las_api.cu", "las_kernels.cu", "las_split.cu"]
+SOURCES = ["las_api.cu", "las_kernels.cu", "las_split.cu", "las_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -24,7 +24,7 @@ EXPORTS = ["las_create", "las_destroy", "las_set_stream", "las_sync", "las_devic
            "las_split_gemm_workspace", "las_split_gemm", "las_energy_grad_batched",
            "las_autotune", "las_df_jk_density", "las_frag_ao2mo", "las_veff",
            "las_split_gemm_noalloc", "las_selftest_bounded_wait", "las_orbital_hvp",
-           "las_status_str"]
+           "las_probe_fp64", "las_status_str"]
 
 
 class LasError(RuntimeError):
@@ -87,6 +87,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.las_veff.restype = i
     lib.las_orbital_hvp.argtypes = [vp] * 8
     lib.las_orbital_hvp.restype = i
+    lib.las_probe_fp64.argtypes = [ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double), vp]
+    lib.las_probe_fp64.restype = i
     lib.las_selftest_bounded_wait.argtypes = [vp]
     lib.las_selftest_bounded_wait.restype = i
     lib.las_kernel_launches.argtypes = []
@@ -356,6 +359,17 @@ def selftest_bounded_wait(stream=None) -> int:
     lib = load_library()
     st = (stream or torch.cuda.current_stream()).cuda_stream
     return int(lib.las_selftest_bounded_wait(st))
+
+
+def probe_fp64(stream=None) -> tuple[float, float]:
+    """Measured FP64 rates of the current device in TFLOP/s: (tensor-core MMA, fused
+    multiply-add), from the library's register-resident probe loops."""
+    import torch
+    lib = load_library()
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib.las_probe_fp64(ctypes.byref(a), ctypes.byref(b), st), "las_probe_fp64")
+    return a.value, b.value
 
 
 def energy_grad_batched(problems, items, stream=None):
