@@ -269,6 +269,7 @@ struct GraphEntry {
   std::vector<las_batch_item> items;
   cudaStream_t stream;
   cudaGraphExec_t exec;
+  void* probs;   // device descriptions of the grouped products (grouped graphs only)
 };
 static std::mutex g_graph_mu;
 static std::vector<GraphEntry> g_graphs;
@@ -280,6 +281,7 @@ static void drop_graphs_of(las_ctx* x) {
     for (las_ctx* c : g_graphs[i].ctxs) hit |= (c == x);
     if (hit) {
       cudaGraphExecDestroy(g_graphs[i].exec);
+      if (g_graphs[i].probs) cudaFree(g_graphs[i].probs);
       g_graphs.erase(g_graphs.begin() + i);
     } else {
       ++i;
@@ -870,6 +872,148 @@ static bool same_items(const las_batch_item& a, const las_batch_item& b) {
          a.dEdC == b.dEdC;
 }
 
+// The batch in split precision as phases: each phase runs every problem's small kernels (digit
+// slicing, per-aux contractions, reductions) on the branch streams, and the split products those
+// kernels feed are recorded instead of launched; after the phase's join, all of them run as ONE
+// persistent grouped launch (tiles in the order the problems are visited: largest first), then
+// the next phase forks again.  Per auxiliary chunk c of each problem:
+//   A: [c = 0: C_occ and h digits]      products: S1 of chunk c (+ h C_occ at c = 0)
+//   B: digits of H                      products: S2 of chunk c (+ C_occ^T h C_occ at c = 0)
+//   C: per-aux contractions, W digits   products: projection of chunk c
+//   D: ordered sum of the projection's partials (run with the next round's A)
+// then the energy and gradient assembly.  Problems with fewer chunks drop out of later rounds.
+struct BatchPlan {
+  int nsys, nb;
+  const std::vector<int>* order;    // problems, largest first
+  const std::vector<int>* branch;   // branch stream of each problem
+  cudaStream_t cs;                  // the capture stream
+  cudaStream_t* br;                 // [nb] branch streams
+  cudaEvent_t fork_ev;
+  cudaEvent_t* join_ev;             // [nb]
+};
+
+static las_status plan_fork(const BatchPlan& P) {
+  cudaError_t e = cudaEventRecord(P.fork_ev, P.cs);
+  for (int b = 0; b < P.nb && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(P.br[b], P.fork_ev, 0);
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "graph fork", __FILE__, __LINE__);
+    return LAS_ERR_CUDA;
+  }
+  return LAS_OK;
+}
+
+static las_status plan_join(const BatchPlan& P) {
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < P.nb && e == cudaSuccess; ++b) {
+    e = cudaEventRecord(P.join_ev[b], P.br[b]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P.cs, P.join_ev[b], 0);
+  }
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "graph join", __FILE__, __LINE__);
+    return LAS_ERR_CUDA;
+  }
+  return LAS_OK;
+}
+
+static int batch_rounds(int nsys, las_ctx* const* ctxs) {
+  int rounds = 0;
+  for (int i = 0; i < nsys; ++i)
+    rounds = std::max(rounds, (ctxs[i]->X + ctxs[i]->Lc - 1) / ctxs[i]->Lc);
+  return rounds;
+}
+
+// Device bytes reserved per grouped launch: at most two products per problem.
+static size_t batch_slot_bytes(int nsys) {
+  return (ozgroup_bytes(2 * (size_t)nsys) + 255) / 256 * 256;
+}
+
+static las_status capture_grouped(const BatchPlan& P, las_ctx* const* ctxs,
+                                  const las_batch_item* items, void* dev,
+                                  std::vector<OzGroup*>* groups) {
+  const int nsys = P.nsys;
+  const int rounds = batch_rounds(nsys, ctxs);
+  const size_t slot = batch_slot_bytes(nsys);
+  std::vector<int> ks(nsys, 1);
+  // run `fn(i, x)` for every problem on its branch (products recorded into a new group when
+  // `record`), join, run the group as one launch, fork again
+  auto phase = [&](auto fn, bool record) -> las_status {
+    OzGroup* g = nullptr;
+    if (record) {
+      g = ozgroup_new();
+      groups->push_back(g);
+      ozgroup_record(g);
+    }
+    las_status r = LAS_OK;
+    for (int k = 0; k < nsys && r == LAS_OK; ++k) {
+      const int i = (*P.order)[k];
+      las_ctx* x = ctxs[i];
+      cudaStream_t saved = x->stream;
+      x->stream = P.br[(*P.branch)[i]];
+      r = fn(i, x);
+      x->stream = saved;
+    }
+    if (record) ozgroup_record(nullptr);
+    if (r != LAS_OK) return r;
+    if ((r = plan_join(P)) != LAS_OK) return r;
+    if (record && (r = ozgroup_launch(g, (uint8_t*)dev + (groups->size() - 1) * slot, P.cs)) !=
+                      LAS_OK)
+      return r;
+    return plan_fork(P);
+  };
+  auto nchunks = [](las_ctx* x) { return (x->X + x->Lc - 1) / x->Lc; };
+  las_status rc = plan_fork(P);
+  for (int c = 0; c < rounds && rc == LAS_OK; ++c) {
+    // A: the previous chunk's partial sums; at c = 0 the C_occ and h digits and h C_occ;
+    //    S1 of chunk c
+    rc = phase([&](int i, las_ctx* x) -> las_status {
+      if (c > 0 && c - 1 < nchunks(x))
+        split_project_reduce(x->split, ks[i], x->Out, c - 1 > 0, x->stream);
+      if (c >= nchunks(x)) return LAS_OK;
+      las_status r = LAS_OK;
+      if (c == 0) {
+        launch_pack_cocc(items[i].C, x->n, x->nmo, x->o, x->op, x->Cocc, x->stream);
+        if ((r = split_prepare_C(x->split, x->Cocc, x->stream)) != LAS_OK) return r;
+        if ((r = split_one_electron_hc(x->split, items[i].h, x->hC, x->stream)) != LAS_OK)
+          return r;
+      }
+      const int l0 = c * x->Lc, nL = std::min(x->Lc, x->X - l0);
+      return split_half(x->split, l0, nL, x->op, x->Ht, x->stream);
+    }, true);
+    if (rc != LAS_OK) break;
+    // B: digits of H; S2 of chunk c (and C_occ^T h C_occ at c = 0)
+    rc = phase([&](int i, las_ctx* x) -> las_status {
+      if (c >= nchunks(x)) return LAS_OK;
+      const int nL = std::min(x->Lc, x->X - c * x->Lc);
+      las_status r = split_full(x->split, nL, x->Ht, x->T, x->stream);
+      if (r == LAS_OK && c == 0) r = split_one_electron_hmo(x->split, x->hC, x->hmo, x->stream);
+      return r;
+    }, true);
+    if (rc != LAS_OK) break;
+    // C: per-aux contractions and W digits; projection of chunk c
+    rc = phase([&](int i, las_ctx* x) -> las_status {
+      if (c >= nchunks(x)) return LAS_OK;
+      const int l0 = c * x->Lc, nL = std::min(x->Lc, x->X - l0);
+      launch_per_aux(x->T, nL, x->op, items[i].dm1s, items[i].dm2, x->fi, x->W, x->eps + l0,
+                     x->vc + l0, x->va + l0, 1, split_hexp(x->split), x->status, x->stream);
+      las_status r = check_launch();
+      if (r == LAS_OK) r = split_project_gemm(x->split, nL, x->W, &ks[i], x->stream);
+      return r;
+    }, true);
+  }
+  // the last chunk's partial sums, then energy and gradient assembly
+  if (rc == LAS_OK)
+    rc = phase([&](int i, las_ctx* x) -> las_status {
+      const int last = nchunks(x) - 1;
+      split_project_reduce(x->split, ks[i], x->Out, last > 0, x->stream);
+      launch_energy_final(x->eps, x->X, x->hmo, x->op, items[i].dm1s, x->fi, items[i].E,
+                          x->stream);
+      launch_assemble_grad(x->Out, x->hC, items[i].dm1s, x->fi, x->n, x->nmo, x->op,
+                           items[i].dEdC, x->stream);
+      return check_launch();
+    }, false);
+  return rc;
+}
+
 extern "C" las_status las_energy_grad_batched(int nsys, las_ctx* const* ctxs,
                                               const las_batch_item* items, void* stream) {
   if (nsys < 0 || (nsys > 0 && (!ctxs || !items))) return LAS_ERR_ARG;
@@ -892,12 +1036,12 @@ extern "C" las_status las_energy_grad_batched(int nsys, las_ctx* const* ctxs,
       return LAS_OK;
     }
   }
-  // capture the systems' chains on private streams (the caller's stream may be the legacy
-  // default stream, which cannot be captured): a fork into LAS_BRANCHES branch streams, each
-  // running its share of the systems in order, and a join, so that the chains of different
-  // systems overlap on the GPU (small systems' grids leave most SMs to the others); systems are
-  // shared out largest first to the branch with the least work so far; the graph is then
-  // launched on `st`
+  // capture on private streams (the caller's stream may be the legacy default stream, which
+  // cannot be captured): forks into LAS_BRANCHES branch streams and joins, so that the small
+  // kernels of different systems overlap on the GPU; systems are shared out largest first to
+  // the branch with the least work so far; the graph is then launched on `st`.
+  // Split precision: the phases of capture_grouped, each product kind of all systems as one
+  // persistent grouped launch.  Otherwise (native FP64): each system's whole chain on its branch.
   constexpr int LAS_BRANCHES = 8;
   static cudaStream_t cap_stream[64], br_stream[64][LAS_BRANCHES];
   static cudaEvent_t fork_ev[64], join_ev[64][LAS_BRANCHES];
@@ -930,42 +1074,49 @@ extern "C" las_status las_energy_grad_batched(int nsys, las_ctx* const* ctxs,
       load[b] += cost(i);
     }
   }
-  LAS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  las_status rc = LAS_OK;
-  cudaError_t ce = cudaEventRecord(fork_ev[dev], cs);
-  for (int b = 0; b < nb && ce == cudaSuccess; ++b)
-    ce = cudaStreamWaitEvent(br_stream[dev][b], fork_ev[dev], 0);
+  bool grouped = true;
+  for (int i = 0; i < nsys; ++i) grouped &= (ctxs[i]->prec == LAS_SPLIT_BF16);
+  void* probs = nullptr;   // device descriptions of the grouped products
+  if (grouped)
+    LAS_CUDA_TRY(cudaMalloc(&probs, 3 * (size_t)batch_rounds(nsys, ctxs) * batch_slot_bytes(nsys)));
+  BatchPlan P{nsys, nb, &order, &branch, cs, br_stream[dev], fork_ev[dev], join_ev[dev]};
+  std::vector<OzGroup*> groups;
+  cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (ce != cudaSuccess) {
-    las_record_cuda_error(ce, "graph fork", __FILE__, __LINE__);
-    rc = LAS_ERR_CUDA;
+    if (probs) cudaFree(probs);
+    las_record_cuda_error(ce, "cudaStreamBeginCapture", __FILE__, __LINE__);
+    return LAS_ERR_CUDA;
   }
-  for (int k = 0; k < nsys && rc == LAS_OK; ++k) {
-    const int i = order[k];
-    las_ctx* x = ctxs[i];
-    cudaStream_t saved = x->stream;
-    const int timing = x->timing;
-    x->stream = br_stream[dev][branch[i]];
-    x->timing = 0;
-    rc = evaluate(x, items[i].C, items[i].h, items[i].dm1s, items[i].dm2, items[i].E,
-                  items[i].dEdC, nullptr);
-    x->stream = saved;
-    x->timing = timing;
-  }
-  for (int b = 0; b < nb && rc == LAS_OK; ++b) {
-    ce = cudaEventRecord(join_ev[dev][b], br_stream[dev][b]);
-    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, join_ev[dev][b], 0);
-    if (ce != cudaSuccess) {
-      las_record_cuda_error(ce, "graph join", __FILE__, __LINE__);
-      rc = LAS_ERR_CUDA;
+  las_status rc = LAS_OK;
+  if (grouped) {
+    rc = capture_grouped(P, ctxs, items, probs, &groups);
+  } else {
+    rc = plan_fork(P);
+    for (int k = 0; k < nsys && rc == LAS_OK; ++k) {
+      const int i = order[k];
+      las_ctx* x = ctxs[i];
+      cudaStream_t saved = x->stream;
+      const int timing = x->timing;
+      x->stream = br_stream[dev][branch[i]];
+      x->timing = 0;
+      rc = evaluate(x, items[i].C, items[i].h, items[i].dm1s, items[i].dm2, items[i].E,
+                    items[i].dEdC, nullptr);
+      x->stream = saved;
+      x->timing = timing;
     }
+    if (rc == LAS_OK) rc = plan_join(P);
   }
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &graph);
-  if (rc != LAS_OK) {
+  // the grouped launches read their product descriptions from `probs`: write them now
+  const size_t slot = batch_slot_bytes(nsys);
+  for (size_t gi = 0; gi < groups.size() && rc == LAS_OK && e == cudaSuccess; ++gi)
+    rc = ozgroup_upload(groups[gi], (uint8_t*)probs + gi * slot);
+  for (OzGroup* g : groups) ozgroup_free(g);
+  if (rc != LAS_OK || e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
-    return rc;
-  }
-  if (e != cudaSuccess) {
+    if (probs) cudaFree(probs);
+    if (rc != LAS_OK) return rc;
     las_record_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__);
     return LAS_ERR_CUDA;
   }
@@ -973,6 +1124,7 @@ extern "C" las_status las_energy_grad_batched(int nsys, las_ctx* const* ctxs,
   e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
+    if (probs) cudaFree(probs);
     las_record_cuda_error(e, "cudaGraphInstantiate", __FILE__, __LINE__);
     return LAS_ERR_CUDA;
   }
@@ -981,6 +1133,7 @@ extern "C" las_status las_energy_grad_batched(int nsys, las_ctx* const* ctxs,
   g.items.assign(items, items + nsys);
   g.stream = st;
   g.exec = exec;
+  g.probs = probs;
   g_graphs.push_back(g);
   LAS_CUDA_TRY(cudaGraphLaunch(exec, st));
   return LAS_OK;

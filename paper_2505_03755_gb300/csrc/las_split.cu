@@ -9,18 +9,21 @@
 //     of 2^-8q of magnitude at most 2^24 * 2^-8q when a group is flushed every 256 values of k,
 //     so the FP32 tensor-core accumulator loses nothing; each flush is added, as an integer, into
 //     an int64 fixed-point accumulator;
-//   * groups q = 4, 5 (weights 2^-32 and 2^-40) share one FP32 accumulator.  (The tensor core's
-//     FP32 accumulation of products of very different weights is measurably less accurate than
-//     IEEE rounding, which is why weight 2^-24 is kept in the exact part.)
+//   * groups q = 4, 5 (weights 2^-32 and 2^-40) each have one FP32 accumulator over the whole
+//     K range of a tile.  (The tensor core's FP32 accumulation of products of very different
+//     weights is measurably less accurate than IEEE rounding, which is why weight 2^-24 is kept
+//     in the exact part and every accumulator holds one weight only.)
 // The recombination uses integer arithmetic only (FP64 arithmetic is slow on this part): the
-// fixed-point sum and the rounded FP32 tail are merged into one int64 and turned into an FP64
-// value by building its bit pattern.  The chosen digit count and pair set follow the split-product
+// fixed-point sum and the two rounded FP32 tails are merged into one int64 and turned into an
+// FP64 value by building its bit pattern.  The chosen digit count and pair set follow the split-product
 // ("Ozaki") scheme for emulating a higher precision with low-precision products.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "las_split.cuh"
 #include "sm100_ptx.cuh"
@@ -29,31 +32,51 @@ namespace lasdf_split {
 
 constexpr int NDIG = 6;
 constexpr int BM = 128;          // rows per CTA tile (tcgen05 M)
-constexpr int BN = 96;           // columns per CTA tile (tcgen05 N)
 constexpr int BK = 16;           // K per pipeline stage (one 32-byte swizzle row of BF16)
-constexpr int NSTAGE = 5;
 constexpr int NEXACT = 4;        // exact weight groups q = 0..3
+constexpr int NGROUP = 6;        // weight groups q = s + t = 0..5 kept (21 digit pairs)
+constexpr int COL_TAIL_GROUP = NEXACT;   // the tail accumulator follows the exact ones
 constexpr int CHUNK = 16;        // stages per exact chunk (256 values of k)
 constexpr int A_PLANE = BM * BK * 2;                 // 4096 B
-constexpr int B_PLANE = BN * BK * 2;                 // 3072 B
 constexpr int A_BYTES = NDIG * A_PLANE;              // 24576
-constexpr int B_BYTES = NDIG * B_PLANE;              // 18432
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;       // 43008 (42 KiB)
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256;
 constexpr int TMEM_COLS = 512;
-constexpr int COL_EXACT0 = 0;    // exact groups q = 0..3 at 0, 96, 192, 288; tail at 384
-constexpr int COL_TAIL = NEXACT * BN;
 constexpr int EPI_WARPS = 16;    // epilogue warps: 4 column groups x 4 TMEM lane quarters
-constexpr int EPI_COLS = BN * 4 / EPI_WARPS;   // 24 accumulator columns per epilogue thread
-constexpr int EPI_STEP = 8;      // columns per TMEM load
-static_assert(EPI_COLS == 3 * EPI_STEP, "three loads per accumulator slice");
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;   // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
-constexpr uint32_t IDESC = sm100::idesc_bf16(BM, BN);
+
+// Tile width BN (columns of the output per CTA tile) and everything that depends on it.  The
+// exact weight groups q = 0..3 each own one FP32 accumulator of BN TMEM columns, at column q*BN,
+// and the tail groups 4 and 5 share one more, at column 4*BN (5*BN <= 512 columns).  The six B
+// digit planes of a stage lie back to back in shared memory (plane t at t*BN rows), so that one
+// MMA of A_s against planes t0..t1 of B (N = (t1-t0+1)*BN <= 256) lands every product A_s B_t in
+// the accumulator of its own exact group s + t (mma_slab): the ten exact products of a stage take
+// six MMAs, four of them of N = 2*BN.  (Narrower tiles with a second tail accumulator, so that
+// the tail products could be merged the same way, measured slower: a shorter stage carries the
+// same waits for data and for the drains of the exact groups.)
+template <int BN_>
+struct OzTile {
+  static constexpr int BN = BN_;
+  static_assert(BN % 16 == 0 && (NEXACT + 1) * BN <= TMEM_COLS, "tile width");
+  static constexpr int B_PLANE = BN * BK * 2;
+  static constexpr int B_BYTES = NDIG * B_PLANE;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int NSTAGE = (220 * 1024) / STAGE_BYTES < 6 ? (220 * 1024) / STAGE_BYTES : 6;
+  static constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256;
+  static constexpr int MAXP = 256 / BN;          // B planes per MMA (N <= 256)
+  // epilogue: the BN columns as 8-column blocks dealt round-robin to the 4 column groups (every
+  // TMEM load is 8 columns at an 8-aligned column)
+  static constexpr int NBLK = BN / 8;
+  static constexpr int MAXB = (NBLK + 3) / 4;    // blocks per epilogue thread, at most
+  static_assert(BN % 8 == 0, "8-column epilogue blocks");
+  static_assert(STAGE_BYTES % 1024 == 0, "stages stay 1024-byte aligned");
+};
 
 // Digit planes are stored K-blocked: element (s, r, k) of an operand with R rows lives at
 //   s*plane + (k / BK) * (Rpad * BK) + r * BK + (k % BK),   Rpad = R rounded up to ROWPAD,
-// so that every pipeline stage of every tile is one contiguous block per plane.
-constexpr long ROWPAD = 384;     // common multiple of the two tile heights (128, 96)
+// so that every pipeline stage of every tile is one contiguous block per plane.  A tile box that
+// reaches past Rpad reads the next K block's rows (finite digits) or, at the end of a plane, the
+// TMA's zero fill: those rows only feed output rows or columns beyond M or N, which are never
+// stored.
+constexpr long ROWPAD = 384;
 
 struct Planes {
   __nv_bfloat16* p;
@@ -109,11 +132,12 @@ __device__ __forceinline__ double make_double(long long W, int E) {
 }
 
 // Column tiles of row tile i that touch the lower triangle (column tile j with j*BN < (i+1)*BM).
-__host__ __device__ __forceinline__ int lower_tiles_in_row(int i, int ntn) {
-  const int c = ((i + 1) * BM + BN - 1) / BN;
+__host__ __device__ __forceinline__ int lower_tiles_in_row(int i, int ntn, int bn) {
+  const int c = ((i + 1) * BM + bn - 1) / bn;
   return c < ntn ? c : ntn;
 }
 
+template <int BN>
 __device__ __forceinline__ void tile_coords(const OzParams& p, long t, int& m0, int& n0,
                                             int& kb0, int& nkb) {
   const int ntn = (p.N + BN - 1) / BN;
@@ -128,7 +152,8 @@ __device__ __forceinline__ void tile_coords(const OzParams& p, long t, int& m0, 
     // only the tiles that touch the lower triangle are enumerated, so that the persistent CTAs
     // share out the work evenly
     int i = 0;
-    for (int c = lower_tiles_in_row(0, ntn); rem >= c; c = lower_tiles_in_row(++i, ntn)) rem -= c;
+    for (int c = lower_tiles_in_row(0, ntn, BN); rem >= c; c = lower_tiles_in_row(++i, ntn, BN))
+      rem -= c;
     m0 = i * BM;
     n0 = (int)rem * BN;
   }
@@ -136,28 +161,95 @@ __device__ __forceinline__ void tile_coords(const OzParams& p, long t, int& m0, 
   nkb = min(p.kb_total, kb0 + p.kb_per_split) - kb0;
 }
 
+// One product of a grouped launch: its tensor maps, parameters and first tile in the launch's
+// tile order (problems are concatenated; tile0 of problem g+1 = tile0 + tiles of problem g).
+struct OzProblem {   // aligned as its tensor maps
+  CUtensorMap tmA, tmB;
+  OzParams p;
+  long tile0;
+};
+
+// The tile a role works on: its product (parameters and maps) and coordinates.  A role's tiles
+// only ever increase, so the product index moves forward only.
+template <int BN, bool GROUPED>
+struct OzCursor {
+  int g = 0;
+  const OzParams* P = nullptr;
+  const CUtensorMap* ma = nullptr;
+  const CUtensorMap* mb = nullptr;
+  int m0 = 0, n0 = 0, kb0 = 0, nkb = 0;
+  __device__ __forceinline__ bool seek(long t, const OzParams& p1, const CUtensorMap* a1,
+                                       const CUtensorMap* b1, const OzProblem* probs,
+                                       int nprob) {
+    long tl = t;
+    bool moved = P == nullptr;
+    if constexpr (GROUPED) {
+      while (g + 1 < nprob && probs[g + 1].tile0 <= t) {
+        ++g;
+        moved = true;
+      }
+      P = &probs[g].p;
+      ma = &probs[g].tmA;
+      mb = &probs[g].tmB;
+      tl = t - probs[g].tile0;
+    } else {
+      P = &p1;
+      ma = a1;
+      mb = b1;
+    }
+    tile_coords<BN>(*P, tl, m0, n0, kb0, nkb);
+    return moved;
+  }
+};
+
+// D[groups s+t0 .. s+t0+nt-1] (+)= A_s * [B_t0 .. B_t0+nt-1]^T: nt consecutive B planes against
+// one A plane, as ceil(nt / MAXP) MMAs of balanced width.
+template <int BN>
+__device__ __forceinline__ void mma_slab(uint32_t tmem, uint32_t sa, uint32_t sb, int s, int t0,
+                                         int nt, bool accumulate) {
+  using T = OzTile<BN>;
+  const int nm = (nt + T::MAXP - 1) / T::MAXP;
+  int t = t0;
+#pragma unroll
+  for (int j = 0; j < nm; ++j) {
+    const int np = (t0 + nt - t) / (nm - j);
+    sm100::mma_bf16(tmem + (uint32_t)((s + t) * BN), sm100::smem_desc_sw32(sa + s * A_PLANE),
+                    sm100::smem_desc_sw32(sb + t * T::B_PLANE),
+                    sm100::idesc_bf16(BM, np * BN), accumulate ? 1u : 0u);
+    t += np;
+  }
+}
+
 // Persistent CTAs (one per SM) walk the tiles (row tile, column tile, K split).  Roles:
 // warp 0 streams digit-plane stages with TMA, warp 1 issues tcgen05.mma, warps 2..17 drain the
 // TMEM accumulators.  Stage, chunk and tile counters run on across tiles so that the loads of the
 // next tile overlap the last MMAs of the current one, and its MMAs overlap the current tile's
 // conversion and stores.
+// GROUPED: the launch walks the concatenated tiles of nprob products described in global
+// memory (probs); otherwise the one product of the kernel parameters.
+template <int BN, bool GROUPED>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-        OzParams p) {
+        const __grid_constant__ OzParams p1, const OzProblem* __restrict__ probs, int nprob,
+        long ntiles) {
+  using T = OzTile<BN>;
+  constexpr int NSTAGE = T::NSTAGE;
+  constexpr int MAXB = T::MAXB;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + NSTAGE * STAGE_BYTES);
+  uint64_t* bars = (uint64_t*)(smem + NSTAGE * T::STAGE_BYTES);
   uint64_t* full = bars;              // [NSTAGE]
   uint64_t* empty = bars + NSTAGE;    // [NSTAGE]
   uint64_t* accf = bars + 2 * NSTAGE;
   uint64_t* acce = bars + 2 * NSTAGE + 1;
   uint64_t* drain = bars + 2 * NSTAGE + 2;
-  uint64_t* accT = bars + 2 * NSTAGE + 3;   // tail accumulator read out (once per tile)
+  uint64_t* accT = bars + 2 * NSTAGE + 3;   // tail accumulators read out (once per tile)
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * NSTAGE + 4);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long ntiles = p.tiles_z * p.ksplit;
+  // status word for waits outside any tile (the first product's)
+  int* const status0 = GROUPED ? probs[0].p.status : p1.status;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
@@ -170,8 +262,10 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     sm100::mbar_init(drain, 1);
     *abort_flag = 0;
     sm100::fence_mbar_init();
-    sm100::tma_prefetch_desc(&tmA);
-    sm100::tma_prefetch_desc(&tmB);
+    if (!GROUPED) {
+      sm100::tma_prefetch_desc(&tmA);
+      sm100::tma_prefetch_desc(&tmB);
+    }
   }
   if (warp == 1) {
     sm100::tmem_alloc(tmem_slot, TMEM_COLS);
@@ -186,38 +280,45 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     // ---------------- TMA producer ----------------
     long gs = 0;
     bool ok = true;
+    OzCursor<BN, GROUPED> cur;
     for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      int m0, n0, kb0, nkb;
-      tile_coords(p, t, m0, n0, kb0, nkb);
-      for (int i = 0; i < nkb; ++i, ++gs) {
+      if (cur.seek(t, p1, &tmA, &tmB, probs, nprob) && GROUPED) {
+        sm100::tma_prefetch_desc(cur.ma);
+        sm100::tma_prefetch_desc(cur.mb);
+      }
+      const OzParams& p = *cur.P;
+      for (int i = 0; i < cur.nkb; ++i, ++gs) {
         const int st = (int)(gs % NSTAGE);
         if (gs >= NSTAGE && !sm100::mbar_wait(&empty[st], (uint32_t)((gs / NSTAGE) - 1) & 1,
                                               abort_flag, p.status, LAS_ERR_TIMEOUT)) {
           ok = false;
           break;
         }
-        uint8_t* sa = smem + st * STAGE_BYTES;
-        sm100::mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
-        const int kb = kb0 + i;
-        sm100::tma_load_3d(sa, &tmA, &full[st], 0, kb * p.a_rpad + p.a_row0 + m0, 0);
-        sm100::tma_load_3d(sa + A_BYTES, &tmB, &full[st], 0, kb * p.b_rpad + p.b_row0 + n0, 0);
+        uint8_t* sa = smem + st * T::STAGE_BYTES;
+        sm100::mbar_arrive_expect_tx(&full[st], T::STAGE_BYTES);
+        const int kb = cur.kb0 + i;
+        sm100::tma_load_3d(sa, cur.ma, &full[st], 0, kb * p.a_rpad + p.a_row0 + cur.m0, 0);
+        sm100::tma_load_3d(sa + A_BYTES, cur.mb, &full[st], 0,
+                           kb * p.b_rpad + p.b_row0 + cur.n0, 0);
       }
     }
     // never leave the CTA with a bulk copy still writing its shared memory
     for (long g = (gs > NSTAGE ? gs - NSTAGE : 0); g < gs; ++g)
-      sm100::mbar_wait(&full[g % NSTAGE], (uint32_t)(g / NSTAGE) & 1, abort_flag, p.status,
+      sm100::mbar_wait(&full[g % NSTAGE], (uint32_t)(g / NSTAGE) & 1, abort_flag, status0,
                        LAS_ERR_TIMEOUT);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    // Per stage the tail MMAs are issued at once; the exact-group MMAs of the first stages of a
-    // chunk may be deferred (their stages stay resident) until the epilogue has drained the
-    // previous chunk, so that the drain overlaps tensor work.
+    // Per stage the tail MMAs (groups 4 and 5) are issued at once; the exact-group MMAs of the
+    // first stages of a chunk may be deferred (their stages stay resident) until the epilogue
+    // has drained the previous chunk, so that the drain overlaps tensor work.
     long gs = 0, gc = 0, tcount = 0;
     bool ok = true, need_acce = false;
+    OzCursor<BN, GROUPED> cur;
     for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      int m0, n0, kb0, nkb;
-      tile_coords(p, t, m0, n0, kb0, nkb);
-      // the tail accumulator of the previous tile must have been read out
+      cur.seek(t, p1, &tmA, &tmB, probs, nprob);
+      const OzParams& p = *cur.P;
+      const int nkb = cur.nkb;
+      // the tail accumulators of the previous tile must have been read out
       if (tcount > 0) {
         if (!sm100::mbar_wait(accT, (uint32_t)(tcount - 1) & 1, abort_flag, p.status,
                               LAS_ERR_TIMEOUT)) {
@@ -237,14 +338,18 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
         }
         sm100::tc_fence_after();
         {
-          const uint32_t sa = sm100::smem_u32(smem + st * STAGE_BYTES);
+          const uint32_t sa = sm100::smem_u32(smem + st * T::STAGE_BYTES);
           const uint32_t sb = sa + A_BYTES;
+          // tail: the 11 products of groups 4 and 5 into the one tail accumulator, started at
+          // the first stage of a tile
           bool tail_acc = (i > 0);
+#pragma unroll
           for (int s = 0; s < NDIG; ++s)
-            for (int t2 = (s >= NEXACT ? 0 : NEXACT - s); s + t2 <= NDIG - 1; ++t2) {
-              sm100::mma_bf16(tmem + COL_TAIL, sm100::smem_desc_sw32(sa + s * A_PLANE),
-                              sm100::smem_desc_sw32(sb + t2 * B_PLANE), IDESC,
-                              tail_acc ? 1u : 0u);
+#pragma unroll
+            for (int t = (s >= NEXACT ? 0 : NEXACT - s); s + t < NGROUP; ++t) {
+              sm100::mma_bf16(tmem + COL_TAIL_GROUP * BN, sm100::smem_desc_sw32(sa + s * A_PLANE),
+                              sm100::smem_desc_sw32(sb + t * T::B_PLANE),
+                              sm100::idesc_bf16(BM, BN), tail_acc ? 1u : 0u);
               tail_acc = true;
             }
         }
@@ -271,23 +376,19 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
           pend0 = gs;
           pend_i0 = i;
         }
-        // exact weights q = 0..3 for the deferred stages and this one, in stage order
+        // exact groups q = 0..3 for the deferred stages and this one, in stage order: A_s
+        // against planes 0 .. 3-s; s = 0 spans all four groups and starts them at a chunk's
+        // first stage
         for (int j = 0; j <= npend; ++j) {
           const long g2 = pend0 + j;
           const int i2 = pend_i0 + j;
           const int st2 = (int)(g2 % NSTAGE);
           const bool first_in_chunk = (i2 % CHUNK) == 0;
-          const uint32_t sa = sm100::smem_u32(smem + st2 * STAGE_BYTES);
+          const uint32_t sa = sm100::smem_u32(smem + st2 * T::STAGE_BYTES);
           const uint32_t sb = sa + A_BYTES;
-          for (int q = 0; q < NEXACT; ++q) {
-            bool started = !first_in_chunk;
-            for (int s = 0; s <= q; ++s) {
-              sm100::mma_bf16(tmem + COL_EXACT0 + q * BN, sm100::smem_desc_sw32(sa + s * A_PLANE),
-                              sm100::smem_desc_sw32(sb + (q - s) * B_PLANE), IDESC,
-                              started ? 1u : 0u);
-              started = true;
-            }
-          }
+#pragma unroll
+          for (int s = 0; s < NEXACT; ++s)
+            mma_slab<BN>(tmem, sa, sb, s, 0, NEXACT - s, s > 0 || !first_in_chunk);
           sm100::mma_commit(&empty[st2]);
         }
         npend = 0;
@@ -301,22 +402,25 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     }
     // make sure no MMA is still writing TMEM when the CTA tears down
     sm100::mma_commit(drain);
-    sm100::mbar_wait(drain, 0, abort_flag, p.status, LAS_ERR_TIMEOUT);
+    sm100::mbar_wait(drain, 0, abort_flag, status0, LAS_ERR_TIMEOUT);
   } else if (warp >= 2) {
     // ---------------- epilogue (16 warps) ----------------
     const int lq = warp & 3;                 // TMEM lane quarter this warp may access
-    const int cg = (warp - 2) >> 2;          // columns [cg*EPI_COLS, (cg+1)*EPI_COLS)
-    const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + cg * EPI_COLS;
-    const float tscale = __int_as_float((127 + 8 * (NEXACT - 1) + p.sh) << 23);  // 2^(24+sh)
+    const int cg = (warp - 2) >> 2;          // column blocks cg, cg + 4, cg + 8, ... of 8
+    const int nb = (T::NBLK - cg + 3) / 4;   // this warp's blocks (warp-uniform)
+    const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16);
     long gc = 0;
     bool ok = true;
+    OzCursor<BN, GROUPED> cur;
     for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      int m0, n0, kb0, nkb;
-      tile_coords(p, t, m0, n0, kb0, nkb);
+      cur.seek(t, p1, &tmA, &tmB, probs, nprob);
+      const OzParams& p = *cur.P;
+      const int m0 = cur.m0, n0 = cur.n0, kb0 = cur.kb0, nkb = cur.nkb;
+      const float tscale = __int_as_float((127 + 8 * (NEXACT - 1) + p.sh) << 23);  // 2^(24+sh)
       const int nchunks = (nkb + CHUNK - 1) / CHUNK;
-      unsigned long long acc[EPI_COLS];
+      unsigned long long acc[MAXB * 8];
 #pragma unroll
-      for (int j = 0; j < EPI_COLS; ++j) acc[j] = 0;
+      for (int j = 0; j < MAXB * 8; ++j) acc[j] = 0;
       for (int c = 0; c < nchunks; ++c, ++gc) {
         if (!sm100::mbar_wait(accf, (uint32_t)gc & 1, abort_flag, p.status, LAS_ERR_TIMEOUT,
                               256)) {
@@ -329,17 +433,20 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
         if (fin) {
           // tail first, so that the next tile's tail MMAs can start:
           // acc <- acc * 2^sh + rint(tail * 2^(24+sh))  (int64, modulo 2^64)
-          uint32_t r[3][EPI_STEP];
 #pragma unroll
-          for (int j = 0; j < 3; ++j) sm100::tmem_ld8(tl + COL_TAIL + j * EPI_STEP, r[j]);
-          sm100::tmem_wait_ld();
+          for (int b = 0; b < MAXB; ++b) {
+            if (b < nb) {
+              const uint32_t col = (uint32_t)((cg + 4 * b) * 8);
+              uint32_t r[8];
+              sm100::tmem_ld8(tl + COL_TAIL_GROUP * BN + col, r);
+              sm100::tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int e = 0; e < EPI_STEP; ++e)
-              acc[j * EPI_STEP + e] =
-                  (acc[j * EPI_STEP + e] << p.sh) +
-                  (unsigned long long)__float2ll_rn(__uint_as_float(r[j][e]) * tscale);
+              for (int e = 0; e < 8; ++e)
+                acc[b * 8 + e] =
+                    (acc[b * 8 + e] << p.sh) +
+                    (unsigned long long)__float2ll_rn(__uint_as_float(r[e]) * tscale);
+            }
+          }
           sm100::tc_fence_before();
           __syncwarp();
           if (lane == 0) sm100::mbar_arrive(accT);
@@ -349,20 +456,22 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
         // V = ((g_0 2^8 + g_1) 2^8 + g_2) 2^8 + g_3 (the first step fits 32 bits)
         static_assert(NEXACT == 4, "the merge below is written for four exact groups");
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          uint32_t r[NEXACT][EPI_STEP];
+        for (int b = 0; b < MAXB; ++b) {
+          if (b < nb) {
+            const uint32_t col = (uint32_t)((cg + 4 * b) * 8);
+            uint32_t r[NEXACT][8];
 #pragma unroll
-          for (int q = 0; q < NEXACT; ++q)
-            sm100::tmem_ld8(tl + COL_EXACT0 + q * BN + j * EPI_STEP, r[q]);
-          sm100::tmem_wait_ld();
+            for (int q = 0; q < NEXACT; ++q) sm100::tmem_ld8(tl + q * BN + col, r[q]);
+            sm100::tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < EPI_STEP; ++e) {
-            const int g0 = __float2int_rn(__uint_as_float(r[0][e]));
-            const int g1 = __float2int_rn(__uint_as_float(r[1][e]) * 256.0f);
-            const int g2 = __float2int_rn(__uint_as_float(r[2][e]) * 65536.0f);
-            const int g3 = __float2int_rn(__uint_as_float(r[3][e]) * 16777216.0f);
-            const long long v = (long long)(g0 * 256 + g1) * 65536 + (long long)g2 * 256 + g3;
-            acc[j * EPI_STEP + e] += (unsigned long long)v << extra;
+            for (int e = 0; e < 8; ++e) {
+              const int g0 = __float2int_rn(__uint_as_float(r[0][e]));
+              const int g1 = __float2int_rn(__uint_as_float(r[1][e]) * 256.0f);
+              const int g2 = __float2int_rn(__uint_as_float(r[2][e]) * 65536.0f);
+              const int g3 = __float2int_rn(__uint_as_float(r[3][e]) * 16777216.0f);
+              const long long v = (long long)(g0 * 256 + g1) * 65536 + (long long)g2 * 256 + g3;
+              acc[b * 8 + e] += (unsigned long long)v << extra;
+            }
           }
         }
         sm100::tc_fence_before();
@@ -380,15 +489,20 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
       }
       const int z = kb0 / p.kb_per_split;
 #pragma unroll
-      for (int j = 0; j < EPI_COLS; ++j) {
-        const int col = n0 + cg * EPI_COLS + j;
-        if (row < p.M && col < p.N) {
-          const int E = ea + p.eb[col] - 14 - 8 * (NEXACT - 1) - p.sh;
-          const double v = make_double((long long)acc[j], E);
-          if (p.mode == 0)
-            p.out[(long)z * p.zstride + (long)row * p.ldc + col] = v;
-          else
-            p.out[(L * p.ht_op + col) * (long)p.ht_n + mu] = v;
+      for (int b = 0; b < MAXB; ++b) {
+        if (b < nb) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int col = n0 + (cg + 4 * b) * 8 + e;
+            if (row < p.M && col < p.N) {
+              const int E = ea + p.eb[col] - 14 - 8 * (NEXACT - 1) - p.sh;
+              const double v = make_double((long long)acc[b * 8 + e], E);
+              if (p.mode == 0)
+                p.out[(long)z * p.zstride + (long)row * p.ldc + col] = v;
+              else
+                p.out[(L * p.ht_op + col) * (long)p.ht_n + mu] = v;
+            }
+          }
         }
       }
     }
@@ -754,15 +868,29 @@ static las_status make_plane_map(CUtensorMap* m, const Planes& P, int box_rows) 
   return r == CUDA_SUCCESS ? LAS_OK : LAS_ERR_INTERNAL;
 }
 
-// The launch attribute is a per-device setting: set once for each device that uses the kernel
+// Tile width of every product: 96 columns, so that the four exact accumulators and the tail
+// take 480 of the 512 TMEM columns.
+constexpr int OZ_BN = 96;
+
+// The launch attribute is a per-device setting: set once for each device that uses the kernels
 // (a repeated set from two threads is harmless).
+template <int BN>
+static cudaError_t ozaki_attr() {
+  cudaError_t e = cudaFuncSetAttribute(k_ozaki<BN, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       OzTile<BN>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ozaki<BN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             OzTile<BN>::SMEM_BYTES);
+  return e;
+}
+
 static las_status ozaki_prepare() {
   static volatile int done[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LAS_ERR_CUDA;
   if (done[dev]) return LAS_OK;
-  cudaError_t e = cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       SMEM_BYTES);
+  cudaError_t e = ozaki_attr<OZ_BN>();
   if (e != cudaSuccess) {
     las_record_cuda_error(e, "cudaFuncSetAttribute(k_ozaki)", __FILE__, __LINE__);
     return LAS_ERR_CUDA;
@@ -784,15 +912,16 @@ static int num_sms() {
   return nsm;
 }
 
+
 // out = A * B^T over K: rows [a_row0, a_row0 + M) of A (row exponents ea, or 0 when null),
 // rows [b_row0, b_row0 + N) of B (row exponents eb: the column exponents of the product).
 // mode 0: out[z*zstride + r*ldc + c] (z = K split); mode 1: Ht layout (rows (L, mu)).
 // Output tiles of an M x N product per K split (lower: only those touching the lower triangle).
-static long ozaki_tiles(long M, long N, int lower) {
-  const long ntm = (M + BM - 1) / BM, ntn = (N + BN - 1) / BN;
+static long ozaki_tiles(long M, long N, int lower, int bn = OZ_BN) {
+  const long ntm = (M + BM - 1) / BM, ntn = (N + bn - 1) / bn;
   if (!lower) return ntm * ntn;
   long t = 0;
-  for (long i = 0; i < ntm; ++i) t += lower_tiles_in_row((int)i, (int)ntn);
+  for (long i = 0; i < ntm; ++i) t += lower_tiles_in_row((int)i, (int)ntn, bn);
   return t;
 }
 
@@ -813,6 +942,48 @@ static int balanced_ksplit(long tiles, long kb, long cap) {
   return best;
 }
 
+// Products recorded instead of launched while a group is being recorded on this host thread.
+struct OzGroup {
+  std::vector<OzProblem> probs;
+  long tiles = 0;
+};
+static thread_local OzGroup* g_record = nullptr;
+
+OzGroup* ozgroup_new() { return new OzGroup(); }
+void ozgroup_free(OzGroup* g) { delete g; }
+void ozgroup_record(OzGroup* g) { g_record = g; }
+size_t ozgroup_count(const OzGroup* g) { return g ? g->probs.size() : 0; }
+size_t ozgroup_bytes(size_t nprob) { return nprob * sizeof(OzProblem); }
+
+// One persistent launch over every recorded product (tiles concatenated in recording order);
+// `dev` is device memory for the product descriptions, filled by ozgroup_upload before the
+// launch runs (the launch may be captured into a graph first).
+las_status ozgroup_launch(const OzGroup* g, void* dev, cudaStream_t st) {
+  if (!g || g->probs.empty()) return LAS_OK;
+  if (!dev || ((uintptr_t)dev % alignof(OzProblem))) return LAS_ERR_INTERNAL;
+  OzParams dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  CUtensorMap m0;
+  memset(&m0, 0, sizeof(m0));
+  dim3 grid((unsigned)std::min<long>(g->tiles, num_sms()), 1, 1);
+  k_ozaki<OZ_BN, true><<<grid, NTHREADS, OzTile<OZ_BN>::SMEM_BYTES, st>>>(
+      m0, m0, dummy, (const OzProblem*)dev, (int)g->probs.size(), g->tiles);
+  las_count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "k_ozaki grouped launch", __FILE__, __LINE__);
+    return LAS_ERR_CUDA;
+  }
+  return LAS_OK;
+}
+
+las_status ozgroup_upload(const OzGroup* g, void* dev) {
+  if (!g || g->probs.empty()) return LAS_OK;
+  LAS_CUDA_TRY(cudaMemcpy(dev, g->probs.data(), g->probs.size() * sizeof(OzProblem),
+                          cudaMemcpyHostToDevice));
+  return LAS_OK;
+}
+
 las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const Planes& B,
                       long b_row0, const int* eb, long N, long K, int ksplit, int mode,
                       double* out, long ldc, long zstride, int ht_n, int ht_op, int* status,
@@ -822,10 +993,12 @@ las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const
     return LAS_ERR_INTERNAL;
   las_status s = ozaki_prepare();
   if (s != LAS_OK) return s;
-  CUtensorMap ma, mb;
-  if ((s = make_plane_map(&ma, A, BM)) != LAS_OK) return s;
-  if ((s = make_plane_map(&mb, B, BN)) != LAS_OK) return s;
-  OzParams p;
+  const int bn = OZ_BN;
+  OzProblem pr;
+  memset(&pr, 0, sizeof(pr));
+  if ((s = make_plane_map(&pr.tmA, A, BM)) != LAS_OK) return s;
+  if ((s = make_plane_map(&pr.tmB, B, bn)) != LAS_OK) return s;
+  OzParams& p = pr.p;
   p.M = (int)M;
   p.N = (int)N;
   p.a_rpad = (int)A.Rpad;
@@ -847,15 +1020,22 @@ las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const
   p.ht_n = ht_n;
   p.ht_op = ht_op;
   p.lower = lower;
-  p.tiles_z = ozaki_tiles(M, N, lower);
+  p.tiles_z = ozaki_tiles(M, N, lower, bn);
   // fractional bits kept for the tail: |fixed-point sum| < 2^38 * (k per CTA) must fit 62 bits
   int lgk = 0;
   while ((1L << lgk) < (long)p.kb_per_split * BK) ++lgk;
   p.sh = std::max(0, std::min(20, 61 - 14 - 8 * (NEXACT - 1) - lgk));
   p.status = status;
   const long tiles = p.tiles_z * ksplit;
+  if (g_record) {   // part of a grouped launch
+    pr.tile0 = g_record->tiles;
+    g_record->tiles += tiles;
+    g_record->probs.push_back(pr);
+    return LAS_OK;
+  }
   dim3 grid((unsigned)std::min<long>(tiles, num_sms()), 1, 1);   // persistent: one CTA per SM
-  k_ozaki<<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, p);
+  k_ozaki<OZ_BN, false><<<grid, NTHREADS, OzTile<OZ_BN>::SMEM_BYTES, st>>>(pr.tmA, pr.tmB, p,
+                                                                          nullptr, 0, tiles);
   las_count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -1100,8 +1280,8 @@ las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaSt
                     0, 0, s->status, st);
 }
 
-las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, int accumulate,
-                         cudaStream_t st) {
+las_status split_project_gemm(SplitState* s, int nL, const double* Wt, int* ks_used,
+                              cudaStream_t st) {
   const long R = (long)nL * s->op;      // K of the projection: (L, p); a multiple of 16
   // the transposed digit planes of H (HdigT) were written by split_full
   // W rows q (K = (L,p)), already scaled by 2^Hexp[(L,p)] and stored transposed: Wt[q][R]
@@ -1111,10 +1291,21 @@ las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, i
   las_status rc = slice_rows(acc, W, s->Wexp, st, s->mx, true);
   if (rc != LAS_OK) return rc;
   const int ks = (int)std::max(1L, std::min((long)s->ks, (R + 32 * 64 - 1) / (32 * 64)));
-  rc = ozaki_gemm(s->HdigT, 0, nullptr, s->n, W, 0, s->Wexp, s->op, R, ks, 0, s->part, s->op,
-                  (long)s->n * s->op, 0, 0, s->status, st);
-  if (rc != LAS_OK) return rc;
+  *ks_used = ks;
+  return ozaki_gemm(s->HdigT, 0, nullptr, s->n, W, 0, s->Wexp, s->op, R, ks, 0, s->part, s->op,
+                    (long)s->n * s->op, 0, 0, s->status, st);
+}
+
+void split_project_reduce(SplitState* s, int ks, double* Out, int accumulate, cudaStream_t st) {
   launch_reduce_partials(s->part, ks, (long)s->n * s->op, Out, accumulate, st);
+}
+
+las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, int accumulate,
+                         cudaStream_t st) {
+  int ks = 1;
+  las_status rc = split_project_gemm(s, nL, Wt, &ks, st);
+  if (rc != LAS_OK) return rc;
+  split_project_reduce(s, ks, Out, accumulate, st);
   return LAS_OK;
 }
 
@@ -1157,20 +1348,31 @@ las_status split_exchange(SplitState* s, int nL, int oc, const double* Ht, doubl
   return LAS_OK;
 }
 
-las_status split_one_electron(SplitState* s, const double* h, double* hC, double* hmo,
-                              cudaStream_t st) {
+las_status split_one_electron_hc(SplitState* s, const double* h, double* hC, cudaStream_t st) {
   // hC = h C_occ  (rows mu of h, columns p of C_occ: the digits of C_occ are already sliced)
   las_status rc = slice_rows(RowsStrided{h, s->n, 1, nullptr}, s->hdig, s->hexp, st, nullptr,
                              true);
   if (rc == LAS_OK)
     rc = ozaki_gemm(s->hdig, 0, s->hexp, s->n, s->Cdig, 0, s->Cexp, s->op, s->n, 1, 0, hC, s->op,
                     0, 0, 0, s->status, st);
+  return rc;
+}
+
+las_status split_one_electron_hmo(SplitState* s, const double* hC, double* hmo,
+                                  cudaStream_t st) {
   // hmo = C_occ^T hC  (rows p of C_occ^T are the C_occ digit rows; columns q of hC)
-  if (rc == LAS_OK)
-    rc = slice_rows(RowsStrided{hC, 1, s->op, nullptr}, s->hcdig, s->hcexp, st, nullptr, true);
+  las_status rc =
+      slice_rows(RowsStrided{hC, 1, s->op, nullptr}, s->hcdig, s->hcexp, st, nullptr, true);
   if (rc == LAS_OK)
     rc = ozaki_gemm(s->Cdig, 0, s->Cexp, s->op, s->hcdig, 0, s->hcexp, s->op, s->n, 1, 0, hmo,
                     s->op, 0, 0, 0, s->status, st);
+  return rc;
+}
+
+las_status split_one_electron(SplitState* s, const double* h, double* hC, double* hmo,
+                              cudaStream_t st) {
+  las_status rc = split_one_electron_hc(s, h, hC, st);
+  if (rc == LAS_OK) rc = split_one_electron_hmo(s, hC, hmo, st);
   return rc;
 }
 

@@ -35,6 +35,30 @@ las_status split_one_electron(SplitState* s, const double* h, double* hC, double
 // Out (+)= sum_{(L,p)} H(mu,(L,p)) W((L,p),q) with Wt[q][(L,p)] = W_L(p,q) * 2^exp(L,p)
 las_status split_project(SplitState* s, int nL, const double* Wt, double* Out, int accumulate,
                          cudaStream_t st);
+// The same in two steps: digits of W and the split-K product into the partial buffer (ks_used
+// receives the K split), then the ordered sum of the partials into Out.
+las_status split_project_gemm(SplitState* s, int nL, const double* Wt, int* ks_used,
+                              cudaStream_t st);
+void split_project_reduce(SplitState* s, int ks, double* Out, int accumulate, cudaStream_t st);
+// hC = h C_occ, then hmo = C_occ^T hC (split_one_electron = both)
+las_status split_one_electron_hc(SplitState* s, const double* h, double* hC, cudaStream_t st);
+las_status split_one_electron_hmo(SplitState* s, const double* hC, double* hmo,
+                                  cudaStream_t st);
+
+// Grouped launches: while a group is being recorded on the calling host thread, every split
+// product of the functions above is appended to it instead of being launched; ozgroup_launch then
+// runs all of them as one persistent launch whose CTAs walk the products' tiles in recording
+// order.  The product descriptions live in device memory `dev` (at least ozgroup_bytes(count)
+// bytes, 128-byte aligned), written by ozgroup_upload before the launch executes (the launch
+// itself may be captured into a CUDA graph first).
+struct OzGroup;
+OzGroup* ozgroup_new();
+void ozgroup_free(OzGroup* g);
+void ozgroup_record(OzGroup* g);   // nullptr: launch products again
+size_t ozgroup_count(const OzGroup* g);
+size_t ozgroup_bytes(size_t nprob);
+las_status ozgroup_launch(const OzGroup* g, void* dev, cudaStream_t st);
+las_status ozgroup_upload(const OzGroup* g, void* dev);
 
 // Fragment-embedding AO2MO (Eqs. ao2mo_1, ao2mo_2, ppaa, papa) in split precision: digit planes
 // of M, of the chunk's half transform and of the slices of T that feed the two integral products.

@@ -113,3 +113,28 @@ def test_batched_many_systems_share_branches():
     assert np.abs(got[0][1] - ref["G"]).max() <= 1e-8
     for L in las:
         L.close()
+
+
+def test_batched_fp64_contexts_per_system_chains():
+    """Native FP64 contexts are captured as whole per-system chains on the branches (no split
+    products to group): bit-identical to single calls and at the FP64 bars against the oracle."""
+    torch = torch_cuda()
+    from paper_2505_03755_gb300 import LasDF, energy_grad_batched
+    systems = _systems(3, lambda sp: sorted(sp, key=lambda x: x["nao"]))
+    las, items = [], []
+    for s in systems:
+        las.append(LasDF(dev(s.Bp), s.nao, s.naux, s.nmo, s.ncore, s.nact, precision="fp64"))
+        items.append((dev(s.C), dev(s.h), dev(s.dm1s_flat()), dev(s.dm2_flat()),
+                      torch.empty((), dtype=torch.float64, device="cuda"),
+                      torch.empty((s.nao, s.nmo), dtype=torch.float64, device="cuda")))
+    energy_grad_batched(las, items)
+    torch.cuda.synchronize()
+    for s, L, it in zip(systems, las, items):
+        e0, g0 = float(it[4]), it[5].cpu().numpy()
+        E, G = L.energy_grad(*it[:4])
+        L.sync()
+        assert float(E) == e0 and np.array_equal(G.cpu().numpy(), g0)
+        ref = O.system_energy_grad(s)
+        assert abs(e0 - ref["E"]) <= 1e-10 * abs(ref["E"])
+        assert np.abs(g0 - ref["G"]).max() <= 1e-9
+        L.close()
