@@ -160,6 +160,7 @@ class LasDF:
         self.nact = list(nact)
         self.precision = precision
         self._B = B_packed  # keep the referenced device buffer alive
+        self._device = B_packed.device
         if B_packed.numel() != naux * nao * (nao + 1) // 2:
             raise ValueError("B_packed must hold naux * nao(nao+1)/2 values")
         arr = (ctypes.c_int * max(1, len(self.nact)))(*self.nact)
@@ -187,8 +188,8 @@ class LasDF:
             return None
         _shape_check(t, shape, name)
         p = _ptr(t)
-        if t.device != self._B.device:
-            raise ValueError(f"{name}: on {t.device}, the context is on {self._B.device}")
+        if t.device != self._device:
+            raise ValueError(f"{name}: on {t.device}, the context is on {self._device}")
         return p
 
     def _state_args(self, C, h, dm1s, dm2):
@@ -207,6 +208,19 @@ class LasDF:
             self.close()
         except Exception:
             pass
+
+    def release_packed_B(self) -> None:
+        """Drop this object's reference to the packed Cholesky vectors.  A split-precision context
+        keeps its own digit planes of B, so its energy, gradient, transform and fragment AO2MO
+        calls never read B_packed again; the JK calls (df_jk, df_jk_density, veff) still do and
+        raise after this call.  FP64 contexts read B_packed in every call and cannot release it."""
+        if self.precision == "fp64":
+            raise ValueError("an FP64 context reads B_packed in every call")
+        self._B = None
+
+    def _need_B(self, what: str) -> None:
+        if self._B is None:
+            raise ValueError(f"{what} reads B_packed, which this context has released")
 
     def device_bytes(self) -> int:
         return int(self._lib.las_device_bytes(self._h))
@@ -270,6 +284,7 @@ class LasDF:
 
     def df_jk(self, C, J=None, K=None):
         import torch
+        self._need_B("df_jk")
         n = self.nao
         J = torch.empty((n, n), dtype=torch.float64, device=C.device) if J is None else J
         K = torch.empty((n, n), dtype=torch.float64, device=C.device) if K is None else K
@@ -281,6 +296,7 @@ class LasDF:
     def df_jk_density(self, Cx, w, J=None, K=None):
         """J and K of D = Cx diag(w) Cx^T (Cx: n x r, w: r; device float64 tensors)."""
         import torch
+        self._need_B("df_jk_density")
         n = self.nao
         J = torch.empty((n, n), dtype=torch.float64, device=Cx.device) if J is None else J
         K = torch.empty((n, n), dtype=torch.float64, device=Cx.device) if K is None else K
@@ -310,6 +326,7 @@ class LasDF:
         """Effective potentials v_sigma = J[gamma_a + gamma_b] - K[gamma_sigma] (Eqs. v_emb,
         vself) of gamma_sigma = C_sigma diag(w_sigma) C_sigma^T (device float64 tensors)."""
         import torch
+        self._need_B("veff")
         n, dev = self.nao, C_alpha.device
         va = torch.empty((n, n), dtype=torch.float64, device=dev)
         vb = torch.empty((n, n), dtype=torch.float64, device=dev)

@@ -150,3 +150,29 @@ def test_split_df_transform_chunked_nao400():
     assert np.abs(lmu.cpu().numpy() - rmu).max() <= 1e-11 * np.abs(rmu).max()
     assert np.abs(lpu.cpu().numpy() - rpu).max() <= 1e-11 * np.abs(rpu).max()
     las.close()
+
+
+def test_split_context_releases_packed_B():
+    """A split context keeps its own digit planes of B: after release_packed_B (and the buffer
+    freed) the energy and gradient are unchanged, and the JK calls, which read B_packed,
+    refuse instead of reading freed memory."""
+    torch = torch_cuda()
+    from gpu_common import SMALL
+    from paper_2505_03755_gb300 import LasDF
+    s = SMALL["ragged"]()
+    B = dev(s.Bp)
+    las = LasDF(B, s.nao, s.naux, s.nmo, s.ncore, s.nact, precision="split")
+    args = (dev(s.C), dev(s.h), dev(s.dm1s_flat()), dev(s.dm2_flat()))
+    E0, G0 = las.energy_grad(*args)
+    las.sync()
+    e0, g0 = float(E0), G0.cpu().numpy()
+    las.release_packed_B()
+    del B
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    E1, G1 = las.energy_grad(*args)
+    las.sync()
+    assert float(E1) == e0 and np.array_equal(G1.cpu().numpy(), g0)
+    with pytest.raises(ValueError):
+        las.df_jk(args[0])
+    las.close()
