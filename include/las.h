@@ -203,11 +203,20 @@ typedef struct {
 las_status las_energy_grad_batched(int nsys, las_ctx* const* ctxs, const las_batch_item* items,
                                    void* stream);
 
-/* Autotuner: times one full evaluation per candidate split-K factor of the projection GEMM
- * (S5/S6) and keeps the fastest for this context (split mode; no-op in FP64 mode).  Writes E and
+/* Autotuner (split mode; no-op in FP64 mode): by timing whole evaluations with per-stage CUDA
+ * events, chooses for this context the tile width (64 or 96 output columns) of each product kind
+ * -- the half transform S1, the full transform S2, the projection S5/S6 and the one-electron
+ * products -- and then the split-K factor of the projection, keeping the fastest of each.  The
+ * choices apply to every later call of the context, batched evaluations included.  Writes E and
  * dEdC as a side effect.  Synchronous. */
 las_status las_autotune(las_ctx* ctx, const double* C, const double* h, const double* dm1s,
                         const double* dm2, double* E, double* dEdC);
+
+/* Tile widths of the split products of a context (bn4: host int[4], for S1, S2, projection and
+ * one-electron products; each 64 or 96), as chosen by las_autotune or set by hand.  Split mode
+ * only (LAS_ERR_UNSUPPORTED otherwise). */
+las_status las_get_tiles(const las_ctx* ctx, int* bn4);
+las_status las_set_tiles(las_ctx* ctx, const int* bn4);
 
 /* Per-stage device times (milliseconds), averaged over the evaluations run since timing was
  * enabled with las_set_timing(ctx, 1) or since the last las_stage_times call (up to the last

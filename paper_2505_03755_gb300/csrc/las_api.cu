@@ -1140,7 +1140,8 @@ extern "C" las_status las_energy_grad_batched(int nsys, las_ctx* const* ctxs,
 }
 
 // ------------------------------------------------------------------------------------------
-// Autotuner: the split-K factor of the projection GEMM, chosen by timing
+// Autotuner: tile widths of the split products and the split-K factor of the projection, chosen
+// by timing whole evaluations
 // ------------------------------------------------------------------------------------------
 extern "C" las_status las_autotune(las_ctx* x, const double* C, const double* h,
                                    const double* dm1s, const double* dm2, double* E,
@@ -1149,30 +1150,77 @@ extern "C" las_status las_autotune(las_ctx* x, const double* C, const double* h,
   if (x->prec != LAS_SPLIT_BF16) return LAS_OK;   // the FP64 path is bound by FP64 arithmetic
   las_status st = las_set_timing(x, 1);
   if (st != LAS_OK) return st;
-  // powers-of-two-ish ladder plus the factor that balances the tiles over the SMs
-  const int cands[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64,
-                       split_balanced_ksplit(x->split, x->Lc)};
-  int best = split_get_ksplit(x->split);
-  float best_ms = 1e30f;
-  for (int ks : cands) {
-    split_set_ksplit(x->split, ks);
-    // two runs: the second is timed
-    for (int r = 0; r < 2; ++r) {
-      if ((st = evaluate(x, C, h, dm1s, dm2, E, dEdC, nullptr)) != LAS_OK) break;
-      if (r == 0) {
-        float dummy[8];
-        las_stage_times(x, dummy, 8);
+  // stage times of one evaluation with the current settings (the second of two runs)
+  auto timed = [&](float* ms) -> las_status {
+    las_status r = LAS_OK;
+    for (int k = 0; k < 2 && r == LAS_OK; ++k) {
+      r = evaluate(x, C, h, dm1s, dm2, E, dEdC, nullptr);
+      if (r == LAS_OK && k == 0) {
+        float d[8];
+        las_stage_times(x, d, 8);
       }
     }
-    if (st != LAS_OK) break;
-    float ms[8] = {0};
-    if (las_stage_times(x, ms, 8) >= 4 && ms[3] < best_ms) {
-      best_ms = ms[3];
-      best = ks;
+    if (r == LAS_OK && las_stage_times(x, ms, 8) < 5) r = LAS_ERR_INTERNAL;
+    return r;
+  };
+  // tile width of each product kind, judged by the stage that holds it: [0] S1, [1] S2 and the
+  // H slicer, [3] the projection, [4] the one-electron products, energy and assembly
+  const int stage_of[SPLIT_NKIND] = {0, 1, 3, 4};
+  const int widths[] = {96, 64};
+  for (int kind = 0; kind < SPLIT_NKIND && st == LAS_OK; ++kind) {
+    int best = split_get_tile(x->split, kind);
+    float best_ms = 1e30f;
+    for (int bn : widths) {
+      if ((st = split_set_tile(x->split, kind, bn)) != LAS_OK) break;
+      float ms[8] = {0};
+      if ((st = timed(ms)) != LAS_OK) break;
+      if (ms[stage_of[kind]] < best_ms) {
+        best_ms = ms[stage_of[kind]];
+        best = bn;
+      }
     }
+    if (st == LAS_OK) st = split_set_tile(x->split, kind, best);
   }
-  split_set_ksplit(x->split, best);
+  // split-K factor of the projection: powers-of-two-ish ladder plus the factor that balances its
+  // tiles over the SMs
+  if (st == LAS_OK) {
+    const int cands[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64,
+                         split_balanced_ksplit(x->split, x->Lc)};
+    int best = split_get_ksplit(x->split);
+    float best_ms = 1e30f;
+    for (int ks : cands) {
+      split_set_ksplit(x->split, ks);
+      float ms[8] = {0};
+      if ((st = timed(ms)) != LAS_OK) break;
+      if (ms[3] < best_ms) {
+        best_ms = ms[3];
+        best = ks;
+      }
+    }
+    split_set_ksplit(x->split, best);
+  }
   las_set_timing(x, 0);
   if (st != LAS_OK) return st;
   return las_sync(x);
+}
+
+// Tile widths chosen for a split context (or set by hand): product kinds S1, S2, projection,
+// one-electron.
+extern "C" las_status las_get_tiles(const las_ctx* x, int* bn4) {
+  if (!x || !bn4) return LAS_ERR_ARG;
+  if (x->prec != LAS_SPLIT_BF16) return LAS_ERR_UNSUPPORTED;
+  for (int k = 0; k < SPLIT_NKIND; ++k) bn4[k] = split_get_tile(x->split, k);
+  return LAS_OK;
+}
+
+extern "C" las_status las_set_tiles(las_ctx* x, const int* bn4) {
+  if (!x || !bn4) return LAS_ERR_ARG;
+  if (x->prec != LAS_SPLIT_BF16) return LAS_ERR_UNSUPPORTED;
+  for (int k = 0; k < SPLIT_NKIND; ++k)
+    if (bn4[k] != 64 && bn4[k] != 96) return LAS_ERR_ARG;
+  for (int k = 0; k < SPLIT_NKIND; ++k) {
+    las_status st = split_set_tile(x->split, k, bn4[k]);
+    if (st != LAS_OK) return st;
+  }
+  return LAS_OK;
 }

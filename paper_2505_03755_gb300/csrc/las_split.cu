@@ -35,7 +35,7 @@ constexpr int BM = 128;          // rows per CTA tile (tcgen05 M)
 constexpr int BK = 16;           // K per pipeline stage (one 32-byte swizzle row of BF16)
 constexpr int NEXACT = 4;        // exact weight groups q = 0..3
 constexpr int NGROUP = 6;        // weight groups q = s + t = 0..5 kept (21 digit pairs)
-constexpr int COL_TAIL_GROUP = NEXACT;   // the tail accumulator follows the exact ones
+
 constexpr int CHUNK = 16;        // stages per exact chunk (256 values of k)
 constexpr int A_PLANE = BM * BK * 2;                 // 4096 B
 constexpr int A_BYTES = NDIG * A_PLANE;              // 24576
@@ -43,30 +43,31 @@ constexpr int TMEM_COLS = 512;
 constexpr int EPI_WARPS = 16;    // epilogue warps: 4 column groups x 4 TMEM lane quarters
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;   // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
 
-// Tile width BN (columns of the output per CTA tile) and everything that depends on it.  The
-// exact weight groups q = 0..3 each own one FP32 accumulator of BN TMEM columns, at column q*BN,
-// and the tail groups 4 and 5 share one more, at column 4*BN (5*BN <= 512 columns).  The six B
-// digit planes of a stage lie back to back in shared memory (plane t at t*BN rows), so that one
-// MMA of A_s against planes t0..t1 of B (N = (t1-t0+1)*BN <= 256) lands every product A_s B_t in
-// the accumulator of its own exact group s + t (mma_slab): the ten exact products of a stage take
-// six MMAs, four of them of N = 2*BN.  (Narrower tiles with a second tail accumulator, so that
-// the tail products could be merged the same way, measured slower: a shorter stage carries the
-// same waits for data and for the drains of the exact groups.)
+// Tile width bn (columns of the output per CTA tile, a product's parameter: 64 or 96) and the
+// stage layout, sized for the widest tile BN.  The exact weight groups q = 0..3 each own one
+// FP32 accumulator of bn TMEM columns, at column q*bn, and the tail groups 4 and 5 share one
+// more, at the fixed column TAIL_COL = 4*BN whatever the tile width, so that consecutive tiles
+// of different widths in one launch never put one tile's tail where the previous tile's exact
+// accumulators are still being drained (every accumulator starts at a multiple of 32).  The
+// six B digit planes of a stage lie back to back in shared memory (plane t at t*bn rows), so
+// that one MMA of A_s against planes t0..t1 of B (N = (t1-t0+1)*bn <= 256) lands every product
+// A_s B_t in the accumulator of its own exact group s + t (mma_slab): the ten exact products of a
+// stage take six MMAs at bn = 96 (four of N = 192) and four at bn = 64 (N = 256, 192, 128, 64).
+// (Tiles with a second tail accumulator, so that the tail products could be merged the same way,
+// measured slower: a shorter stage carries the same waits for data and for the exact drains.)
 template <int BN_>
 struct OzTile {
-  static constexpr int BN = BN_;
-  static_assert(BN % 16 == 0 && (NEXACT + 1) * BN <= TMEM_COLS, "tile width");
-  static constexpr int B_PLANE = BN * BK * 2;
+  static constexpr int BN = BN_;   // the widest tile the stage layout holds
+  static_assert(BN % 32 == 0 && (NEXACT + 1) * BN <= TMEM_COLS, "tile width");
+  static constexpr int B_PLANE = BN * BK * 2;    // bytes per B plane at the widest tile
+  static constexpr int TAIL_COL = NEXACT * BN;   // TMEM column of the tail accumulator
   static constexpr int B_BYTES = NDIG * B_PLANE;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int NSTAGE = (220 * 1024) / STAGE_BYTES < 6 ? (220 * 1024) / STAGE_BYTES : 6;
   static constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256;
-  static constexpr int MAXP = 256 / BN;          // B planes per MMA (N <= 256)
-  // epilogue: the BN columns as 8-column blocks dealt round-robin to the 4 column groups (every
-  // TMEM load is 8 columns at an 8-aligned column)
-  static constexpr int NBLK = BN / 8;
-  static constexpr int MAXB = (NBLK + 3) / 4;    // blocks per epilogue thread, at most
-  static_assert(BN % 8 == 0, "8-column epilogue blocks");
+  // epilogue: a tile's bn columns as 8-column blocks dealt round-robin to the 4 column groups
+  // (every TMEM load is 8 columns at an 8-aligned column)
+  static constexpr int MAXB = (BN / 8 + 3) / 4;  // blocks per epilogue thread, at most
   static_assert(STAGE_BYTES % 1024 == 0, "stages stay 1024-byte aligned");
 };
 
@@ -118,6 +119,7 @@ struct OzParams {
   int lower;               // symmetric product: only tiles that touch the lower triangle
   long tiles_z;            // tiles per K split (the lower-triangle ones only when lower != 0)
   int sh;                  // fractional bits kept when merging the tail
+  int bn;                  // tile width: 64 or 96 columns
   int* status;
 };
 
@@ -131,31 +133,31 @@ __device__ __forceinline__ double make_double(long long W, int E) {
   return __longlong_as_double(b + ((long long)E << 52));
 }
 
-// Column tiles of row tile i that touch the lower triangle (column tile j with j*BN < (i+1)*BM).
+// Column tiles of row tile i that touch the lower triangle (column tile j with j*bn < (i+1)*BM).
 __host__ __device__ __forceinline__ int lower_tiles_in_row(int i, int ntn, int bn) {
   const int c = ((i + 1) * BM + bn - 1) / bn;
   return c < ntn ? c : ntn;
 }
 
-template <int BN>
 __device__ __forceinline__ void tile_coords(const OzParams& p, long t, int& m0, int& n0,
                                             int& kb0, int& nkb) {
-  const int ntn = (p.N + BN - 1) / BN;
+  const int bn = p.bn;
+  const int ntn = (p.N + bn - 1) / bn;
   const int z = (int)(t / p.tiles_z);
   long rem = t - (long)z * p.tiles_z;
   // the column tiles of one row tile are adjacent in tile order so that concurrently running
   // CTAs share that row tile's digit planes through L2
   if (!p.lower) {
     m0 = (int)(rem / ntn) * BM;
-    n0 = (int)(rem % ntn) * BN;
+    n0 = (int)(rem % ntn) * bn;
   } else {
     // only the tiles that touch the lower triangle are enumerated, so that the persistent CTAs
     // share out the work evenly
     int i = 0;
-    for (int c = lower_tiles_in_row(0, ntn, BN); rem >= c; c = lower_tiles_in_row(++i, ntn, BN))
+    for (int c = lower_tiles_in_row(0, ntn, bn); rem >= c; c = lower_tiles_in_row(++i, ntn, bn))
       rem -= c;
     m0 = i * BM;
-    n0 = (int)rem * BN;
+    n0 = (int)rem * bn;
   }
   kb0 = z * p.kb_per_split;
   nkb = min(p.kb_total, kb0 + p.kb_per_split) - kb0;
@@ -171,7 +173,7 @@ struct OzProblem {   // aligned as its tensor maps
 
 // The tile a role works on: its product (parameters and maps) and coordinates.  A role's tiles
 // only ever increase, so the product index moves forward only.
-template <int BN, bool GROUPED>
+template <bool GROUPED>
 struct OzCursor {
   int g = 0;
   const OzParams* P = nullptr;
@@ -197,27 +199,56 @@ struct OzCursor {
       ma = a1;
       mb = b1;
     }
-    tile_coords<BN>(*P, tl, m0, n0, kb0, nkb);
+    tile_coords(*P, tl, m0, n0, kb0, nkb);
     return moved;
   }
 };
 
-// D[groups s+t0 .. s+t0+nt-1] (+)= A_s * [B_t0 .. B_t0+nt-1]^T: nt consecutive B planes against
-// one A plane, as ceil(nt / MAXP) MMAs of balanced width.
-template <int BN>
+// D[groups s+t0 .. s+t0+nt-1] (+)= A_s * [B_t0 .. B_t0+nt-1]^T: nt consecutive B planes (tile
+// width BNV, planes BNV*32 bytes apart) against one A plane, as ceil(nt / maxp) MMAs of balanced
+// width (N = np * BNV <= 256).  Everything is a compile-time constant once inlined: the single
+// issuing thread must not spend its time on address arithmetic.
+template <int BNV>
 __device__ __forceinline__ void mma_slab(uint32_t tmem, uint32_t sa, uint32_t sb, int s, int t0,
                                          int nt, bool accumulate) {
-  using T = OzTile<BN>;
-  const int nm = (nt + T::MAXP - 1) / T::MAXP;
+  constexpr int maxp = 256 / BNV;
+  const int nm = (nt + maxp - 1) / maxp;
   int t = t0;
 #pragma unroll
   for (int j = 0; j < nm; ++j) {
     const int np = (t0 + nt - t) / (nm - j);
-    sm100::mma_bf16(tmem + (uint32_t)((s + t) * BN), sm100::smem_desc_sw32(sa + s * A_PLANE),
-                    sm100::smem_desc_sw32(sb + t * T::B_PLANE),
-                    sm100::idesc_bf16(BM, np * BN), accumulate ? 1u : 0u);
+    sm100::mma_bf16(tmem + (uint32_t)((s + t) * BNV), sm100::smem_desc_sw32(sa + s * A_PLANE),
+                    sm100::smem_desc_sw32(sb + t * BNV * BK * 2),
+                    sm100::idesc_bf16(BM, np * BNV), accumulate ? 1u : 0u);
     t += np;
   }
+}
+
+// One stage's tail products (groups 4 and 5, eleven MMAs into the tail accumulator at tail_col),
+// started at the first stage of a tile.
+template <int BNV>
+__device__ __forceinline__ void mma_tail(uint32_t tmem_tail, uint32_t sa, uint32_t sb,
+                                         bool first_stage) {
+  bool acc = !first_stage;
+#pragma unroll
+  for (int s = 0; s < NDIG; ++s)
+#pragma unroll
+    for (int t = (s >= NEXACT ? 0 : NEXACT - s); s + t < NGROUP; ++t) {
+      sm100::mma_bf16(tmem_tail, sm100::smem_desc_sw32(sa + s * A_PLANE),
+                      sm100::smem_desc_sw32(sb + t * BNV * BK * 2), sm100::idesc_bf16(BM, BNV),
+                      acc ? 1u : 0u);
+      acc = true;
+    }
+}
+
+// One stage's exact products (groups 0..3): A_s against planes 0 .. 3-s; s = 0 spans all four
+// groups and starts them at a chunk's first stage.
+template <int BNV>
+__device__ __forceinline__ void mma_exact(uint32_t tmem, uint32_t sa, uint32_t sb,
+                                          bool first_in_chunk) {
+#pragma unroll
+  for (int s = 0; s < NEXACT; ++s)
+    mma_slab<BNV>(tmem, sa, sb, s, 0, NEXACT - s, s > 0 || !first_in_chunk);
 }
 
 // Persistent CTAs (one per SM) walk the tiles (row tile, column tile, K split).  Roles:
@@ -226,8 +257,10 @@ __device__ __forceinline__ void mma_slab(uint32_t tmem, uint32_t sa, uint32_t sb
 // next tile overlap the last MMAs of the current one, and its MMAs overlap the current tile's
 // conversion and stores.
 // GROUPED: the launch walks the concatenated tiles of nprob products described in global
-// memory (probs); otherwise the one product of the kernel parameters.
-template <int BN, bool GROUPED>
+// memory (probs); otherwise the one product of the kernel parameters.  FIXBN: the tile width of
+// every product of the launch as a compile-time constant (64 or 96), or 0 when products of both
+// widths share a grouped launch (each tile then reads its product's width).
+template <int BN, bool GROUPED, int FIXBN>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
         const __grid_constant__ OzParams p1, const OzProblem* __restrict__ probs, int nprob,
@@ -280,7 +313,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     // ---------------- TMA producer ----------------
     long gs = 0;
     bool ok = true;
-    OzCursor<BN, GROUPED> cur;
+    OzCursor<GROUPED> cur;
     for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       if (cur.seek(t, p1, &tmA, &tmB, probs, nprob) && GROUPED) {
         sm100::tma_prefetch_desc(cur.ma);
@@ -295,7 +328,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
           break;
         }
         uint8_t* sa = smem + st * T::STAGE_BYTES;
-        sm100::mbar_arrive_expect_tx(&full[st], T::STAGE_BYTES);
+        sm100::mbar_arrive_expect_tx(&full[st], A_BYTES + NDIG * (FIXBN ? FIXBN : p.bn) * BK * 2);
         const int kb = cur.kb0 + i;
         sm100::tma_load_3d(sa, cur.ma, &full[st], 0, kb * p.a_rpad + p.a_row0 + cur.m0, 0);
         sm100::tma_load_3d(sa + A_BYTES, cur.mb, &full[st], 0,
@@ -313,11 +346,12 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     // has drained the previous chunk, so that the drain overlaps tensor work.
     long gs = 0, gc = 0, tcount = 0;
     bool ok = true, need_acce = false;
-    OzCursor<BN, GROUPED> cur;
+    OzCursor<GROUPED> cur;
     for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       cur.seek(t, p1, &tmA, &tmB, probs, nprob);
       const OzParams& p = *cur.P;
       const int nkb = cur.nkb;
+      const int bn = FIXBN ? FIXBN : p.bn;
       // the tail accumulators of the previous tile must have been read out
       if (tcount > 0) {
         if (!sm100::mbar_wait(accT, (uint32_t)(tcount - 1) & 1, abort_flag, p.status,
@@ -340,18 +374,9 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
         {
           const uint32_t sa = sm100::smem_u32(smem + st * T::STAGE_BYTES);
           const uint32_t sb = sa + A_BYTES;
-          // tail: the 11 products of groups 4 and 5 into the one tail accumulator, started at
-          // the first stage of a tile
-          bool tail_acc = (i > 0);
-#pragma unroll
-          for (int s = 0; s < NDIG; ++s)
-#pragma unroll
-            for (int t = (s >= NEXACT ? 0 : NEXACT - s); s + t < NGROUP; ++t) {
-              sm100::mma_bf16(tmem + COL_TAIL_GROUP * BN, sm100::smem_desc_sw32(sa + s * A_PLANE),
-                              sm100::smem_desc_sw32(sb + t * T::B_PLANE),
-                              sm100::idesc_bf16(BM, BN), tail_acc ? 1u : 0u);
-              tail_acc = true;
-            }
+          // tail: the 11 products of groups 4 and 5 into the one tail accumulator
+          if (bn == 64) mma_tail<64>(tmem + T::TAIL_COL, sa, sb, i == 0);
+          else mma_tail<96>(tmem + T::TAIL_COL, sa, sb, i == 0);
         }
         const bool last_in_chunk = (i % CHUNK) == CHUNK - 1 || i == nkb - 1;
         if (need_acce) {
@@ -386,9 +411,8 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
           const bool first_in_chunk = (i2 % CHUNK) == 0;
           const uint32_t sa = sm100::smem_u32(smem + st2 * T::STAGE_BYTES);
           const uint32_t sb = sa + A_BYTES;
-#pragma unroll
-          for (int s = 0; s < NEXACT; ++s)
-            mma_slab<BN>(tmem, sa, sb, s, 0, NEXACT - s, s > 0 || !first_in_chunk);
+          if (bn == 64) mma_exact<64>(tmem, sa, sb, first_in_chunk);
+          else mma_exact<96>(tmem, sa, sb, first_in_chunk);
           sm100::mma_commit(&empty[st2]);
         }
         npend = 0;
@@ -407,15 +431,16 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     // ---------------- epilogue (16 warps) ----------------
     const int lq = warp & 3;                 // TMEM lane quarter this warp may access
     const int cg = (warp - 2) >> 2;          // column blocks cg, cg + 4, cg + 8, ... of 8
-    const int nb = (T::NBLK - cg + 3) / 4;   // this warp's blocks (warp-uniform)
     const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16);
     long gc = 0;
     bool ok = true;
-    OzCursor<BN, GROUPED> cur;
+    OzCursor<GROUPED> cur;
     for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       cur.seek(t, p1, &tmA, &tmB, probs, nprob);
       const OzParams& p = *cur.P;
       const int m0 = cur.m0, n0 = cur.n0, kb0 = cur.kb0, nkb = cur.nkb;
+      const int bn = FIXBN ? FIXBN : p.bn;
+      const int nb = (bn / 8 - cg + 3) / 4;   // this warp's column blocks (warp-uniform)
       const float tscale = __int_as_float((127 + 8 * (NEXACT - 1) + p.sh) << 23);  // 2^(24+sh)
       const int nchunks = (nkb + CHUNK - 1) / CHUNK;
       unsigned long long acc[MAXB * 8];
@@ -438,7 +463,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
             if (b < nb) {
               const uint32_t col = (uint32_t)((cg + 4 * b) * 8);
               uint32_t r[8];
-              sm100::tmem_ld8(tl + COL_TAIL_GROUP * BN + col, r);
+              sm100::tmem_ld8(tl + T::TAIL_COL + col, r);
               sm100::tmem_wait_ld();
 #pragma unroll
               for (int e = 0; e < 8; ++e)
@@ -461,7 +486,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
             const uint32_t col = (uint32_t)((cg + 4 * b) * 8);
             uint32_t r[NEXACT][8];
 #pragma unroll
-            for (int q = 0; q < NEXACT; ++q) sm100::tmem_ld8(tl + q * BN + col, r[q]);
+            for (int q = 0; q < NEXACT; ++q) sm100::tmem_ld8(tl + q * bn + col, r[q]);
             sm100::tmem_wait_ld();
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
@@ -868,21 +893,19 @@ static las_status make_plane_map(CUtensorMap* m, const Planes& P, int box_rows) 
   return r == CUDA_SUCCESS ? LAS_OK : LAS_ERR_INTERNAL;
 }
 
-// Tile width of every product: 96 columns, so that the four exact accumulators and the tail
-// take 480 of the 512 TMEM columns.
+// Widest tile (the stage layout's B region) and the default tile width of a product: 96
+// columns, so that the four exact accumulators and the tail take 480 of the 512 TMEM columns.
+// A product may run with 64-column tiles instead (las_autotune chooses per product kind).
 constexpr int OZ_BN = 96;
+static bool valid_bn(int bn) { return bn == 64 || bn == 96; }
 
 // The launch attribute is a per-device setting: set once for each device that uses the kernels
 // (a repeated set from two threads is harmless).
-template <int BN>
+template <bool GROUPED, int FIXBN>
 static cudaError_t ozaki_attr() {
-  cudaError_t e = cudaFuncSetAttribute(k_ozaki<BN, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       OzTile<BN>::SMEM_BYTES);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ozaki<BN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             OzTile<BN>::SMEM_BYTES);
-  return e;
+  return cudaFuncSetAttribute(k_ozaki<OZ_BN, GROUPED, FIXBN>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              OzTile<OZ_BN>::SMEM_BYTES);
 }
 
 static las_status ozaki_prepare() {
@@ -890,7 +913,11 @@ static las_status ozaki_prepare() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LAS_ERR_CUDA;
   if (done[dev]) return LAS_OK;
-  cudaError_t e = ozaki_attr<OZ_BN>();
+  cudaError_t e = ozaki_attr<false, 96>();
+  if (e == cudaSuccess) e = ozaki_attr<false, 64>();
+  if (e == cudaSuccess) e = ozaki_attr<true, 96>();
+  if (e == cudaSuccess) e = ozaki_attr<true, 64>();
+  if (e == cudaSuccess) e = ozaki_attr<true, 0>();
   if (e != cudaSuccess) {
     las_record_cuda_error(e, "cudaFuncSetAttribute(k_ozaki)", __FILE__, __LINE__);
     return LAS_ERR_CUDA;
@@ -966,8 +993,18 @@ las_status ozgroup_launch(const OzGroup* g, void* dev, cudaStream_t st) {
   CUtensorMap m0;
   memset(&m0, 0, sizeof(m0));
   dim3 grid((unsigned)std::min<long>(g->tiles, num_sms()), 1, 1);
-  k_ozaki<OZ_BN, true><<<grid, NTHREADS, OzTile<OZ_BN>::SMEM_BYTES, st>>>(
-      m0, m0, dummy, (const OzProblem*)dev, (int)g->probs.size(), g->tiles);
+  int bn = g->probs[0].p.bn;   // one width for the whole launch, or 0: read per product
+  for (const OzProblem& pr : g->probs)
+    if (pr.p.bn != bn) bn = 0;
+  const OzProblem* probs = (const OzProblem*)dev;
+  const int np = (int)g->probs.size();
+  constexpr int SM = OzTile<OZ_BN>::SMEM_BYTES;
+  if (bn == 96)
+    k_ozaki<OZ_BN, true, 96><<<grid, NTHREADS, SM, st>>>(m0, m0, dummy, probs, np, g->tiles);
+  else if (bn == 64)
+    k_ozaki<OZ_BN, true, 64><<<grid, NTHREADS, SM, st>>>(m0, m0, dummy, probs, np, g->tiles);
+  else
+    k_ozaki<OZ_BN, true, 0><<<grid, NTHREADS, SM, st>>>(m0, m0, dummy, probs, np, g->tiles);
   las_count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -987,13 +1024,13 @@ las_status ozgroup_upload(const OzGroup* g, void* dev) {
 las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const Planes& B,
                       long b_row0, const int* eb, long N, long K, int ksplit, int mode,
                       double* out, long ldc, long zstride, int ht_n, int ht_op, int* status,
-                      cudaStream_t st, int lower = 0) {
+                      cudaStream_t st, int lower = 0, int bn = OZ_BN) {
   if (M <= 0 || N <= 0) return LAS_OK;
-  if (a_row0 + M > A.Rpad || b_row0 + N > B.Rpad || K > A.nkb * BK || K > B.nkb * BK)
+  if (a_row0 + M > A.Rpad || b_row0 + N > B.Rpad || K > A.nkb * BK || K > B.nkb * BK ||
+      !valid_bn(bn))
     return LAS_ERR_INTERNAL;
   las_status s = ozaki_prepare();
   if (s != LAS_OK) return s;
-  const int bn = OZ_BN;
   OzProblem pr;
   memset(&pr, 0, sizeof(pr));
   if ((s = make_plane_map(&pr.tmA, A, BM)) != LAS_OK) return s;
@@ -1025,6 +1062,7 @@ las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const
   int lgk = 0;
   while ((1L << lgk) < (long)p.kb_per_split * BK) ++lgk;
   p.sh = std::max(0, std::min(20, 61 - 14 - 8 * (NEXACT - 1) - lgk));
+  p.bn = bn;
   p.status = status;
   const long tiles = p.tiles_z * ksplit;
   if (g_record) {   // part of a grouped launch
@@ -1034,8 +1072,11 @@ las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const
     return LAS_OK;
   }
   dim3 grid((unsigned)std::min<long>(tiles, num_sms()), 1, 1);   // persistent: one CTA per SM
-  k_ozaki<OZ_BN, false><<<grid, NTHREADS, OzTile<OZ_BN>::SMEM_BYTES, st>>>(pr.tmA, pr.tmB, p,
-                                                                          nullptr, 0, tiles);
+  constexpr int SM = OzTile<OZ_BN>::SMEM_BYTES;
+  if (bn == 64)
+    k_ozaki<OZ_BN, false, 64><<<grid, NTHREADS, SM, st>>>(pr.tmA, pr.tmB, p, nullptr, 0, tiles);
+  else
+    k_ozaki<OZ_BN, false, 96><<<grid, NTHREADS, SM, st>>>(pr.tmA, pr.tmB, p, nullptr, 0, tiles);
   las_count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -1103,6 +1144,7 @@ struct SplitState {
   int* hcexp;            // [op]
   int ksplit6;           // partial buffers allocated for this many K splits
   int ks;                // split-K factor of the projection GEMM (autotunable)
+  int bn[SPLIT_NKIND];   // tile width of each product kind (autotunable): 64 or 96
   int* status;
 };
 
@@ -1131,6 +1173,7 @@ las_status split_create(SplitState** out, int n, int X, int op, int Lc, const do
   s->Lc = Lc;
   s->status = status;
   s->ksplit6 = 64;
+  for (int k = 0; k < SPLIT_NKIND; ++k) s->bn[k] = OZ_BN;
   // one-time launch attributes, so that later calls can be captured into CUDA graphs
   if (ozaki_prepare() != LAS_OK || num_sms() <= 0) {
     free(s);
@@ -1207,8 +1250,15 @@ const int* split_hexp(SplitState* s) { return s->Hexp; }
 
 int split_get_ksplit(SplitState* s) { return s->ks; }
 int split_balanced_ksplit(SplitState* s, int nL) {
-  return balanced_ksplit(ozaki_tiles(s->n, s->op, 0), ((long)nL * s->op + BK - 1) / BK,
+  return balanced_ksplit(ozaki_tiles(s->n, s->op, 0, s->bn[SPLIT_PROJECT]),
+                         ((long)nL * s->op + BK - 1) / BK,
                          std::min<long>(s->ksplit6, std::max(1L, ((long)nL * s->op) / 2048)));
+}
+int split_get_tile(SplitState* s, int kind) { return s->bn[kind]; }
+las_status split_set_tile(SplitState* s, int kind, int bn) {
+  if (kind < 0 || kind >= SPLIT_NKIND || !valid_bn(bn)) return LAS_ERR_ARG;
+  s->bn[kind] = bn;
+  return LAS_OK;
 }
 void split_set_ksplit(SplitState* s, int ks) { s->ks = std::max(1, std::min(ks, s->ksplit6)); }
 
@@ -1259,7 +1309,8 @@ las_status split_half(SplitState* s, int l0, int nL, int oc, double* Ht, cudaStr
   const long rows = (long)nL * s->n;
   if (oc < 1 || oc > s->op) return LAS_ERR_INTERNAL;
   return ozaki_gemm(s->Bdig, (long)l0 * s->n, s->Bexp + (long)l0 * s->n, rows, s->Cdig, 0,
-                    s->Cexp, oc, s->n, 1, 1, Ht, 0, 0, s->n, oc, s->status, st);
+                    s->Cexp, oc, s->n, 1, 1, Ht, 0, 0, s->n, oc, s->status, st, 0,
+                    s->bn[SPLIT_HALF]);
 }
 
 las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaStream_t st) {
@@ -1277,7 +1328,7 @@ las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaSt
     }
   }
   return ozaki_gemm(s->Hdig, 0, s->Hexp, R, s->Cdig, 0, s->Cexp, s->op, s->n, 1, 0, T, s->op, 0,
-                    0, 0, s->status, st);
+                    0, 0, s->status, st, 0, s->bn[SPLIT_FULL]);
 }
 
 las_status split_project_gemm(SplitState* s, int nL, const double* Wt, int* ks_used,
@@ -1293,7 +1344,7 @@ las_status split_project_gemm(SplitState* s, int nL, const double* Wt, int* ks_u
   const int ks = (int)std::max(1L, std::min((long)s->ks, (R + 32 * 64 - 1) / (32 * 64)));
   *ks_used = ks;
   return ozaki_gemm(s->HdigT, 0, nullptr, s->n, W, 0, s->Wexp, s->op, R, ks, 0, s->part, s->op,
-                    (long)s->n * s->op, 0, 0, s->status, st);
+                    (long)s->n * s->op, 0, 0, s->status, st, 0, s->bn[SPLIT_PROJECT]);
 }
 
 void split_project_reduce(SplitState* s, int ks, double* Out, int accumulate, cudaStream_t st) {
@@ -1354,7 +1405,7 @@ las_status split_one_electron_hc(SplitState* s, const double* h, double* hC, cud
                              true);
   if (rc == LAS_OK)
     rc = ozaki_gemm(s->hdig, 0, s->hexp, s->n, s->Cdig, 0, s->Cexp, s->op, s->n, 1, 0, hC, s->op,
-                    0, 0, 0, s->status, st);
+                    0, 0, 0, s->status, st, 0, s->bn[SPLIT_ONE_ELECTRON]);
   return rc;
 }
 
@@ -1365,7 +1416,7 @@ las_status split_one_electron_hmo(SplitState* s, const double* hC, double* hmo,
       slice_rows(RowsStrided{hC, 1, s->op, nullptr}, s->hcdig, s->hcexp, st, nullptr, true);
   if (rc == LAS_OK)
     rc = ozaki_gemm(s->Cdig, 0, s->Cexp, s->op, s->hcdig, 0, s->hcexp, s->op, s->n, 1, 0, hmo,
-                    s->op, 0, 0, 0, s->status, st);
+                    s->op, 0, 0, 0, s->status, st, 0, s->bn[SPLIT_ONE_ELECTRON]);
   return rc;
 }
 

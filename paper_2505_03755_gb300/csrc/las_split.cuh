@@ -24,6 +24,11 @@ las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaSt
 // only the lower triangle (mu >= nu) is valid: mirror it afterwards
 las_status split_exchange(SplitState* s, int nL, int oc, const double* Ht, double* K, int accumulate,
                           cudaStream_t st);
+// Product kinds of an evaluation, each with its own tile width (64 or 96 columns; default 96):
+// S1, S2 (with its H slicer), the projection and the two one-electron products.
+enum { SPLIT_HALF = 0, SPLIT_FULL = 1, SPLIT_PROJECT = 2, SPLIT_ONE_ELECTRON = 3, SPLIT_NKIND = 4 };
+int split_get_tile(SplitState* s, int kind);
+las_status split_set_tile(SplitState* s, int kind, int bn);
 // split-K factor of the projection GEMM (1..64)
 int split_get_ksplit(SplitState* s);
 // split-K of the projection that shares its tiles out most evenly over the SMs for nL aux rows

@@ -24,7 +24,7 @@ EXPORTS = ["las_create", "las_destroy", "las_set_stream", "las_sync", "las_devic
            "las_split_gemm_workspace", "las_split_gemm", "las_energy_grad_batched",
            "las_autotune", "las_df_jk_density", "las_frag_ao2mo", "las_veff",
            "las_split_gemm_noalloc", "las_selftest_bounded_wait", "las_orbital_hvp",
-           "las_probe_fp64", "las_status_str"]
+           "las_probe_fp64", "las_get_tiles", "las_set_tiles", "las_status_str"]
 
 
 class LasError(RuntimeError):
@@ -87,6 +87,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.las_veff.restype = i
     lib.las_orbital_hvp.argtypes = [vp] * 8
     lib.las_orbital_hvp.restype = i
+    lib.las_get_tiles.argtypes = [vp, ctypes.POINTER(i)]
+    lib.las_get_tiles.restype = i
+    lib.las_set_tiles.argtypes = [vp, ctypes.POINTER(i)]
+    lib.las_set_tiles.restype = i
     lib.las_probe_fp64.argtypes = [ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), vp]
     lib.las_probe_fp64.restype = i
@@ -275,12 +279,23 @@ class LasDF:
         return float(E[0]), G
 
     def autotune(self, C, h, dm1s, dm2):
-        """Pick the fastest split-K factor of the projection GEMM for this problem."""
+        """Pick, by timing, the fastest tile width of each split product kind and the fastest
+        split-K factor of the projection GEMM for this problem."""
         import torch
         E = torch.empty((), dtype=torch.float64, device=C.device)
         G = torch.empty((self.nao, self.nmo), dtype=torch.float64, device=C.device)
         _check(self._lib.las_autotune(self._h, *self._state_args(C, h, dm1s, dm2), _ptr(E),
                                       _ptr(G)), "las_autotune")
+
+    def tiles(self) -> list[int]:
+        """Tile widths (64 or 96) of the split products: S1, S2, projection, one-electron."""
+        buf = (ctypes.c_int * 4)()
+        _check(self._lib.las_get_tiles(self._h, buf), "las_get_tiles")
+        return list(buf)
+
+    def set_tiles(self, widths) -> None:
+        buf = (ctypes.c_int * 4)(*[int(w) for w in widths])
+        _check(self._lib.las_set_tiles(self._h, buf), "las_set_tiles")
 
     def df_jk(self, C, J=None, K=None):
         import torch

@@ -43,6 +43,9 @@ def test_batched_graph_matches_individual_and_oracle():
         _systems(2, lambda sp: sorted(sp, key=lambda x: -x["nao"])[20:])
     las, items, batched = _run(systems)
     las[0].autotune(*items[0][:4])
+    # products of different tile widths in the same grouped launches
+    las[1].set_tiles([64, 64, 64, 64])
+    las[2].set_tiles([64, 96, 64, 96])
     batched(las, items)
     torch.cuda.synchronize()
     first = [(float(it[4]), it[5].cpu().numpy()) for it in items]

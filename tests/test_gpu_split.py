@@ -176,3 +176,26 @@ def test_split_context_releases_packed_B():
     with pytest.raises(ValueError):
         las.df_jk(args[0])
     las.close()
+
+
+def test_tile_widths_give_identical_results():
+    """The tile width (64 or 96 output columns) only regroups output columns: every element sums
+    the same digit products in the same order, so the results are bit-identical.  Nao=400
+    (76 occupied orbitals: one 96-column tile or two 64-column tiles)."""
+    torch_cuda()
+    s = workload_system("nao400")
+    las = make_las(s, "split")
+    args = (dev(s.C), dev(s.h), dev(s.dm1s_flat()), dev(s.dm2_flat()))
+    out = {}
+    for widths in ([96, 96, 96, 96], [64, 64, 64, 64], [64, 96, 64, 96]):
+        las.set_tiles(widths)
+        assert las.tiles() == widths
+        E, G = las.energy_grad(*args)
+        las.sync()
+        out[tuple(widths)] = (float(E), G.cpu().numpy())
+    e0, g0 = out[(96, 96, 96, 96)]
+    for e, g in out.values():
+        assert e == e0 and np.array_equal(g, g0)
+    with pytest.raises(Exception):
+        las.set_tiles([80, 96, 96, 96])
+    las.close()
