@@ -120,6 +120,7 @@ struct OzParams {
   long tiles_z;            // tiles per K split (the lower-triangle ones only when lower != 0)
   int sh;                  // fractional bits kept when merging the tail
   int bn;                  // tile width: 64 or 96 columns
+  int a_mn;                // A read MN-major: rows of the stored planes are K, their K is M
   int* status;
 };
 
@@ -208,18 +209,25 @@ struct OzCursor {
 // width BNV, planes BNV*32 bytes apart) against one A plane, as ceil(nt / maxp) MMAs of balanced
 // width (N = np * BNV <= 256).  Everything is a compile-time constant once inlined: the single
 // issuing thread must not spend its time on address arithmetic.
+// Descriptor of A plane s of a stage: K-major, or MN-major (amn) when the stage holds the
+// transposed access of planes stored with rows along K.
+__device__ __forceinline__ uint64_t a_desc(uint32_t sa, int s, bool amn) {
+  return amn ? sm100::smem_desc_sw32_mn(sa + s * A_PLANE) : sm100::smem_desc_sw32(sa + s * A_PLANE);
+}
+
 template <int BNV>
 __device__ __forceinline__ void mma_slab(uint32_t tmem, uint32_t sa, uint32_t sb, int s, int t0,
-                                         int nt, bool accumulate) {
+                                         int nt, bool accumulate, bool amn) {
   constexpr int maxp = 256 / BNV;
   const int nm = (nt + maxp - 1) / maxp;
   int t = t0;
 #pragma unroll
   for (int j = 0; j < nm; ++j) {
     const int np = (t0 + nt - t) / (nm - j);
-    sm100::mma_bf16(tmem + (uint32_t)((s + t) * BNV), sm100::smem_desc_sw32(sa + s * A_PLANE),
+    sm100::mma_bf16(tmem + (uint32_t)((s + t) * BNV), a_desc(sa, s, amn),
                     sm100::smem_desc_sw32(sb + t * BNV * BK * 2),
-                    sm100::idesc_bf16(BM, np * BNV), accumulate ? 1u : 0u);
+                    sm100::idesc_bf16(BM, np * BNV) | (amn ? sm100::IDESC_A_MN : 0u),
+                    accumulate ? 1u : 0u);
     t += np;
   }
 }
@@ -228,15 +236,15 @@ __device__ __forceinline__ void mma_slab(uint32_t tmem, uint32_t sa, uint32_t sb
 // started at the first stage of a tile.
 template <int BNV>
 __device__ __forceinline__ void mma_tail(uint32_t tmem_tail, uint32_t sa, uint32_t sb,
-                                         bool first_stage) {
+                                         bool first_stage, bool amn) {
   bool acc = !first_stage;
+  const uint32_t idesc = sm100::idesc_bf16(BM, BNV) | (amn ? sm100::IDESC_A_MN : 0u);
 #pragma unroll
   for (int s = 0; s < NDIG; ++s)
 #pragma unroll
     for (int t = (s >= NEXACT ? 0 : NEXACT - s); s + t < NGROUP; ++t) {
-      sm100::mma_bf16(tmem_tail, sm100::smem_desc_sw32(sa + s * A_PLANE),
-                      sm100::smem_desc_sw32(sb + t * BNV * BK * 2), sm100::idesc_bf16(BM, BNV),
-                      acc ? 1u : 0u);
+      sm100::mma_bf16(tmem_tail, a_desc(sa, s, amn), sm100::smem_desc_sw32(sb + t * BNV * BK * 2),
+                      idesc, acc ? 1u : 0u);
       acc = true;
     }
 }
@@ -245,10 +253,10 @@ __device__ __forceinline__ void mma_tail(uint32_t tmem_tail, uint32_t sa, uint32
 // groups and starts them at a chunk's first stage.
 template <int BNV>
 __device__ __forceinline__ void mma_exact(uint32_t tmem, uint32_t sa, uint32_t sb,
-                                          bool first_in_chunk) {
+                                          bool first_in_chunk, bool amn) {
 #pragma unroll
   for (int s = 0; s < NEXACT; ++s)
-    mma_slab<BNV>(tmem, sa, sb, s, 0, NEXACT - s, s > 0 || !first_in_chunk);
+    mma_slab<BNV>(tmem, sa, sb, s, 0, NEXACT - s, s > 0 || !first_in_chunk, amn);
 }
 
 // Persistent CTAs (one per SM) walk the tiles (row tile, column tile, K split).  Roles:
@@ -330,7 +338,10 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
         uint8_t* sa = smem + st * T::STAGE_BYTES;
         sm100::mbar_arrive_expect_tx(&full[st], A_BYTES + NDIG * (FIXBN ? FIXBN : p.bn) * BK * 2);
         const int kb = cur.kb0 + i;
-        sm100::tma_load_3d(sa, cur.ma, &full[st], 0, kb * p.a_rpad + p.a_row0 + cur.m0, 0);
+        if (p.a_mn)   // rows of the stored planes are this product's K, their K blocks its M
+          sm100::tma_load_4d(sa, cur.ma, &full[st], 0, p.a_row0 + kb * BK, cur.m0 / BK, 0);
+        else
+          sm100::tma_load_3d(sa, cur.ma, &full[st], 0, kb * p.a_rpad + p.a_row0 + cur.m0, 0);
         sm100::tma_load_3d(sa + A_BYTES, cur.mb, &full[st], 0,
                            kb * p.b_rpad + p.b_row0 + cur.n0, 0);
       }
@@ -352,6 +363,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
       const OzParams& p = *cur.P;
       const int nkb = cur.nkb;
       const int bn = FIXBN ? FIXBN : p.bn;
+      const bool amn = p.a_mn != 0;
       // the tail accumulators of the previous tile must have been read out
       if (tcount > 0) {
         if (!sm100::mbar_wait(accT, (uint32_t)(tcount - 1) & 1, abort_flag, p.status,
@@ -375,8 +387,8 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
           const uint32_t sa = sm100::smem_u32(smem + st * T::STAGE_BYTES);
           const uint32_t sb = sa + A_BYTES;
           // tail: the 11 products of groups 4 and 5 into the one tail accumulator
-          if (bn == 64) mma_tail<64>(tmem + T::TAIL_COL, sa, sb, i == 0);
-          else mma_tail<96>(tmem + T::TAIL_COL, sa, sb, i == 0);
+          if (bn == 64) mma_tail<64>(tmem + T::TAIL_COL, sa, sb, i == 0, amn);
+          else mma_tail<96>(tmem + T::TAIL_COL, sa, sb, i == 0, amn);
         }
         const bool last_in_chunk = (i % CHUNK) == CHUNK - 1 || i == nkb - 1;
         if (need_acce) {
@@ -411,8 +423,8 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
           const bool first_in_chunk = (i2 % CHUNK) == 0;
           const uint32_t sa = sm100::smem_u32(smem + st2 * T::STAGE_BYTES);
           const uint32_t sb = sa + A_BYTES;
-          if (bn == 64) mma_exact<64>(tmem, sa, sb, first_in_chunk);
-          else mma_exact<96>(tmem, sa, sb, first_in_chunk);
+          if (bn == 64) mma_exact<64>(tmem, sa, sb, first_in_chunk, amn);
+          else mma_exact<96>(tmem, sa, sb, first_in_chunk, amn);
           sm100::mma_commit(&empty[st2]);
         }
         npend = 0;
@@ -709,17 +721,15 @@ k_digits_long(Acc acc, Planes P, long rows, long kbc, const unsigned long long* 
   for (int s = 0; s < NDIG; ++s) P.p[P.idx(s, r, k)] = d[s];
 }
 
-// Half-transformed rows (L,p) of Ht [R][n]: exponents, digit planes Hd (rows (L,p), K = mu) and
-// the same digits transposed, HdT (rows mu, K = (L,p)), in one pass.  Block: 16 rows r, 256
-// threads.  The row maxima are read first (warp per row); the digit pass then re-reads the
-// block's rows while they are still in L2: thread (r, c) cuts 8 consecutive columns of row r per
-// 128-column step (a warp's 16-byte stores into Hd cover 512 contiguous bytes), and the
-// transposed tile gives 32-byte stores of the block's 16 rows per column mu into HdT.  Rows of
-// Hd beyond the block's 16 and rows mu >= n of HdT are never written (zero from set-up).
+// Half-transformed rows (L,p) of Ht [R][n]: exponents and digit planes Hd (rows (L,p),
+// K = mu); the full transform reads them K-major and the projection MN-major (rows mu, K =
+// (L,p)), so one layout serves both.  Block: 16 rows r, 256 threads.  The row maxima are read
+// first (warp per row); the digit pass then re-reads the block's rows: thread (r, c) cuts 8
+// consecutive columns of row r per 128-column step (a warp's 16-byte stores into Hd cover 512
+// contiguous bytes).  Rows of Hd beyond R and columns k >= n are written as zero digits within the
+// block's K range; rows beyond the blocks stay zero from set-up.
 __global__ void __launch_bounds__(256)
-k_slice_ht(const double* __restrict__ Ht, long R, int n, Planes Hd, Planes HdT,
-           int* __restrict__ ex) {
-  __shared__ __align__(16) __nv_bfloat16 tile[NDIG][128][24];   // [s][column k][row r] (+8 pad)
+k_slice_ht(const double* __restrict__ Ht, long R, int n, Planes Hd, int* __restrict__ ex) {
   __shared__ int es[16];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long r0 = (long)blockIdx.x * 16;
@@ -746,55 +756,37 @@ k_slice_ht(const double* __restrict__ Ht, long R, int n, Planes Hd, Planes HdT,
   const long kend = Hd.nkb * BK;            // a multiple of 16
   const int rr = threadIdx.x & 15, kc = threadIdx.x >> 4;   // digit pass: row, 8-column group
   const long r = r0 + rr;
+  if (r >= Hd.Rpad) return;
   const bool live = r < R;
   const int e = es[rr];
   const double* hrow = Ht + r * n;
   for (long k0 = 0; k0 < kend; k0 += 128) {
     const long k = k0 + kc * 8;
-    if (k < kend) {
-      double x[8];
-      if (live && (n & 1) == 0 && k + 8 <= n) {
-        // 16-byte loads (rows start 16-byte aligned when n is even)
+    if (k >= kend) break;
+    double x[8];
+    if (live && (n & 1) == 0 && k + 8 <= n) {
+      // 16-byte loads (rows start 16-byte aligned when n is even)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const double2 t = *(const double2*)(hrow + k + 2 * j);
-          x[2 * j] = t.x;
-          x[2 * j + 1] = t.y;
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) x[j] = (live && k + j < n) ? hrow[k + j] : 0.0;
+      for (int j = 0; j < 4; ++j) {
+        const double2 t = *(const double2*)(hrow + k + 2 * j);
+        x[2 * j] = t.x;
+        x[2 * j + 1] = t.y;
       }
-      __nv_bfloat16 d[8][NDIG];
+    } else {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) digits_of(x[j], e, d[j]);
-#pragma unroll
-      for (int s = 0; s < NDIG; ++s) {
-        uint4 v;
-        __nv_bfloat16* pv = (__nv_bfloat16*)&v;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          pv[j] = d[j][s];
-          tile[s][kc * 8 + j][rr] = d[j][s];
-        }
-        if (r < Hd.Rpad) *(uint4*)(Hd.p + Hd.idx(s, r, k)) = v;
-      }
+      for (int j = 0; j < 8; ++j) x[j] = (live && k + j < n) ? hrow[k + j] : 0.0;
     }
-    __syncthreads();
-    // transposed: (plane s, column mu) pairs, 16 rows = 32 bytes each
-    if (r0 + 16 <= HdT.nkb * BK) {
-      for (int q = threadIdx.x; q < NDIG * 128; q += 256) {
-        const int s = q >> 7, kk = q & 127;
-        const long mu = k0 + kk;
-        if (mu < n) {
-          uint4* dst = (uint4*)(HdT.p + HdT.idx(s, mu, r0));
-          const uint4* src = (const uint4*)&tile[s][kk][0];
-          dst[0] = src[0];
-          dst[1] = src[1];
-        }
-      }
+    __nv_bfloat16 d[8][NDIG];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) digits_of(x[j], e, d[j]);
+#pragma unroll
+    for (int s = 0; s < NDIG; ++s) {
+      uint4 v;
+      __nv_bfloat16* pv = (__nv_bfloat16*)&v;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) pv[j] = d[j][s];
+      *(uint4*)(Hd.p + Hd.idx(s, r, k)) = v;
     }
-    __syncthreads();
   }
 }
 
@@ -888,6 +880,26 @@ static las_status make_plane_map(CUtensorMap* m, const Planes& P, int box_rows) 
   cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)NDIG};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)P.p, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? LAS_OK : LAS_ERR_INTERNAL;
+}
+
+// 4D map for reading planes MN-major (as the A operand of a product whose K runs along the
+// stored rows): dims {BK, Rpad, nkb, NDIG}; a box is 16 stored rows (16 values of K) of BM / BK
+// consecutive K blocks of the stored layout (BM values of M), every plane: BM * 32 bytes per
+// plane, as in the K-major case.  Boxes past the last stored K block read the TMA's zero fill.
+static las_status make_plane_map_mn(CUtensorMap* m, const Planes& P) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return LAS_ERR_CUDA;
+  if (((uintptr_t)P.p & 15) || P.Rpad <= 0 || P.Rpad > 0x7FFFFFFFL || P.nkb <= 0)
+    return LAS_ERR_INTERNAL;
+  cuuint64_t dims[4] = {(cuuint64_t)BK, (cuuint64_t)P.Rpad, (cuuint64_t)P.nkb, (cuuint64_t)NDIG};
+  cuuint64_t strides[3] = {(cuuint64_t)BK * 2, (cuuint64_t)P.Rpad * BK * 2,
+                           (cuuint64_t)P.plane * 2};
+  cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)BK, (cuuint32_t)(BM / BK), (cuuint32_t)NDIG};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)P.p, dims, strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? LAS_OK : LAS_ERR_INTERNAL;
@@ -1024,16 +1036,19 @@ las_status ozgroup_upload(const OzGroup* g, void* dev) {
 las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const Planes& B,
                       long b_row0, const int* eb, long N, long K, int ksplit, int mode,
                       double* out, long ldc, long zstride, int ht_n, int ht_op, int* status,
-                      cudaStream_t st, int lower = 0, int bn = OZ_BN) {
+                      cudaStream_t st, int lower = 0, int bn = OZ_BN, int a_mn = 0) {
   if (M <= 0 || N <= 0) return LAS_OK;
-  if (a_row0 + M > A.Rpad || b_row0 + N > B.Rpad || K > A.nkb * BK || K > B.nkb * BK ||
-      !valid_bn(bn))
+  // a_mn: A's stored rows [a_row0, a_row0 + K) are the product's K, its stored K the rows M
+  const bool a_ok = a_mn ? (a_row0 + K <= A.Rpad && M <= A.nkb * BK)
+                         : (a_row0 + M <= A.Rpad && K <= A.nkb * BK);
+  if (!a_ok || b_row0 + N > B.Rpad || K > B.nkb * BK || !valid_bn(bn) || (a_mn && lower))
     return LAS_ERR_INTERNAL;
   las_status s = ozaki_prepare();
   if (s != LAS_OK) return s;
   OzProblem pr;
   memset(&pr, 0, sizeof(pr));
-  if ((s = make_plane_map(&pr.tmA, A, BM)) != LAS_OK) return s;
+  if ((s = a_mn ? make_plane_map_mn(&pr.tmA, A) : make_plane_map(&pr.tmA, A, BM)) != LAS_OK)
+    return s;
   if ((s = make_plane_map(&pr.tmB, B, bn)) != LAS_OK) return s;
   OzParams& p = pr.p;
   p.M = (int)M;
@@ -1063,6 +1078,7 @@ las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const
   while ((1L << lgk) < (long)p.kb_per_split * BK) ++lgk;
   p.sh = std::max(0, std::min(20, 61 - 14 - 8 * (NEXACT - 1) - lgk));
   p.bn = bn;
+  p.a_mn = a_mn;
   p.status = status;
   const long tiles = p.tiles_z * ksplit;
   if (g_record) {   // part of a grouped launch
@@ -1315,10 +1331,7 @@ las_status split_half(SplitState* s, int l0, int nL, int oc, double* Ht, cudaStr
 
 las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaStream_t st) {
   const long R = (long)nL * s->op;
-  // chunk views: same allocations, the chunk's own K extent for the transposed planes
-  Planes HdT = s->HdigT;
-  HdT.K = R;
-  k_slice_ht<<<(unsigned)((R + 15) / 16), 256, 0, st>>>(Ht, R, s->n, s->Hdig, HdT, s->Hexp);
+  k_slice_ht<<<(unsigned)((R + 15) / 16), 256, 0, st>>>(Ht, R, s->n, s->Hdig, s->Hexp);
   las_count_launch();
   {
     cudaError_t e = cudaGetLastError();
@@ -1334,7 +1347,8 @@ las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaSt
 las_status split_project_gemm(SplitState* s, int nL, const double* Wt, int* ks_used,
                               cudaStream_t st) {
   const long R = (long)nL * s->op;      // K of the projection: (L, p); a multiple of 16
-  // the transposed digit planes of H (HdigT) were written by split_full
+  // A: the digit planes of H written by split_full (rows (L,p), K = mu), read MN-major: rows mu,
+  // K = (L,p); their per-(L,p) exponents are folded into W.
   // W rows q (K = (L,p)), already scaled by 2^Hexp[(L,p)] and stored transposed: Wt[q][R]
   Planes W = s->Wdig;
   W.K = R;
@@ -1343,8 +1357,8 @@ las_status split_project_gemm(SplitState* s, int nL, const double* Wt, int* ks_u
   if (rc != LAS_OK) return rc;
   const int ks = (int)std::max(1L, std::min((long)s->ks, (R + 32 * 64 - 1) / (32 * 64)));
   *ks_used = ks;
-  return ozaki_gemm(s->HdigT, 0, nullptr, s->n, W, 0, s->Wexp, s->op, R, ks, 0, s->part, s->op,
-                    (long)s->n * s->op, 0, 0, s->status, st, 0, s->bn[SPLIT_PROJECT]);
+  return ozaki_gemm(s->Hdig, 0, nullptr, s->n, W, 0, s->Wexp, s->op, R, ks, 0, s->part, s->op,
+                    (long)s->n * s->op, 0, 0, s->status, st, 0, s->bn[SPLIT_PROJECT], 1);
 }
 
 void split_project_reduce(SplitState* s, int ks, double* Out, int accumulate, cudaStream_t st) {

@@ -94,6 +94,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* m, uin
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* m, uint64_t* bar,
+                                            int x, int y, int z, int w) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)m), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "r"(w)
+      : "memory");
+}
+
 // ---- tcgen05 -------------------------------------------------------------------------------
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -194,6 +203,22 @@ __device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
   d |= (uint64_t)6 << 61;                          // swizzle: 32-byte
   return d;
 }
+
+// The same for an MN-major operand in the 32-byte swizzle mode: atoms of 16 BF16 along M/N by
+// 8 rows along K; atoms along M/N are 512 bytes apart (leading byte offset), 8-row groups along K
+// 256 bytes apart (stride byte offset).
+__device__ __forceinline__ uint64_t smem_desc_sw32_mn(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)(512 >> 4) << 16;                 // leading byte offset: next 16 along M/N
+  d |= (uint64_t)(256 >> 4) << 32;                 // stride byte offset: next 8 along K
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)6 << 61;                          // swizzle: 32-byte
+  return d;
+}
+
+// Instruction-descriptor bit that reads A MN-major.
+constexpr uint32_t IDESC_A_MN = 1u << 15;
 
 // Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
