@@ -106,14 +106,26 @@ def packed_B(seed: int, n: int, naux: int, out: np.ndarray | None = None,
     return out
 
 
-def packed_B_rows(seed: int, n: int, naux: int, l0: int, l1: int) -> np.ndarray:
+def packed_B_rows(seed: int, n: int, naux: int, l0: int, l1: int,
+                  threads: int | None = None) -> np.ndarray:
     """Rows [l0, l1) of the full-size packed B of `packed_B(seed, n, naux)` (same counters and
-    decay), for checks on a slice of a workload too large to evaluate on the host."""
+    decay): a slice of a workload too large to evaluate on the host, or one rank's block of
+    auxiliary rows."""
     P = npair(n)
     decay = _tril_decay(n)
     out = np.empty((l1 - l0, P), dtype=np.float64)
-    for L in range(l0, l1):
-        out[L - l0] = normals(seed, 0, L * P, P) * decay * np.exp(-L / naux)
+
+    def rows(a: int, b: int) -> None:
+        for L in range(a, b):
+            out[L - l0] = normals(seed, 0, L * P, P) * decay * np.exp(-L / naux)
+
+    threads = threads or min(32, os.cpu_count() or 1)
+    if (l1 - l0) * P < 4_000_000 or threads == 1:
+        rows(l0, l1)
+    else:
+        step = max(1, (l1 - l0 + threads * 4 - 1) // (threads * 4))
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(lambda a: rows(a, min(l1, a + step)), range(l0, l1, step)))
     return out
 
 

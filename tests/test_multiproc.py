@@ -119,3 +119,33 @@ def test_two_rank_aux_sharded_energy_grad_equals_whole_system():
     half = O.energy_grad(s.Bp, s.nao, s.h, s.C, s.ncore, s.dm1s, s.dm2, l0=0, l1=27)
     assert abs(half["E"] - ref["E"]) > 1e-6 * abs(ref["E"])
 
+
+
+def _shard_worker(rank, ws, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    import bench
+    w = dict(nao=11, naux=53, ncore=2, frags=[(2, 2), (2, 3)])
+    s, (l0, l1), _ = bench.make_shard_inputs(rank, ws, w, seed=2024)
+    t = bench.max_over_ranks(0.05 * (rank + 1), ws)
+    out[rank] = (l0, l1, s.Bp.copy(), s.C.copy(), bench.strong_scaling_rate(4, t))
+    dist.destroy_process_group()
+
+
+def test_two_rank_partitioned_bench_inputs():
+    """The bench's L-partition mode: each rank draws exactly its block of auxiliary rows of the
+    same system (identical C on both ranks), the blocks tile the index, and the rate counts the
+    one system's evaluations over the slowest rank's time."""
+    from las_inputs import make_system
+    ws = 2
+    port = _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_shard_worker, args=(ws, port, out), nprocs=ws, join=True)
+    full = make_system(11, 53, 2, [(2, 2), (2, 3)], seed=2024)
+    assert out[0][0] == 0 and out[0][1] == out[1][0] and out[1][1] == 53
+    for r in range(ws):
+        l0, l1, Bp, C, rate = out[r]
+        assert np.array_equal(Bp, full.Bp[l0:l1])
+        assert np.array_equal(C, full.C)
+        assert rate == pytest.approx(4 / 0.1)
