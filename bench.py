@@ -203,7 +203,8 @@ def run_partitioned(args, ws, rank, local):
     for _ in range(args.warmup):
         energy_grad_aux_sharded(las, C, h, d1, d2)
     torch.cuda.synchronize(dev)
-    dist.barrier()
+    if ws > 1:
+        dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -213,7 +214,8 @@ def run_partitioned(args, ws, rank, local):
     e1.record(stream)
     e1.synchronize()
     torch.cuda.synchronize(dev)
-    dist.barrier()
+    if ws > 1:
+        dist.barrier()
     ck = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
     E_val = float(E.item())
@@ -734,10 +736,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="both", choices=["both", "split", "fp64"])
-    ap.add_argument("--partition", default="aux", choices=["aux", "systems"],
-                    help="N > 1: 'aux' splits the one Nao=1200 system along the auxiliary index "
-                         "(one all-reduce per evaluation, strong scaling); 'systems' gives every "
-                         "rank its own system (no collective, weak scaling)")
+    ap.add_argument("--partition", default=None, choices=["aux", "systems"],
+                    help="'aux' (the default for N > 1) splits the one Nao=1200 system along the "
+                         "auxiliary index (one all-reduce per evaluation, strong scaling; with "
+                         "N = 1 the same path on one GPU); 'systems' gives every rank its own "
+                         "system (no collective, weak scaling)")
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--fp64-warmup", type=int, default=3)
     ap.add_argument("--cpu-rows", type=int, default=240,
@@ -815,7 +818,9 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    if ws > 1 and args.partition == "aux":
+    if args.partition is None:
+        args.partition = "aux" if ws > 1 else "systems"
+    if args.partition == "aux":
         r = run_partitioned(args, ws, rank, local)
         if rank == 0:
             w = WORKLOAD
@@ -831,7 +836,8 @@ def main():
                                "[dE/dC, E] per evaluation"),
                 "precision": "split", "E": r["E"], "rank0_rows": list(r["rows"]),
                 "clocks": r["clocks"], "input_generation_s": r["gen_s"]}), flush=True)
-        dist.destroy_process_group()
+        if ws > 1:
+            dist.destroy_process_group()
         return
     s, work, peaks, res, tgen = run_ours(args, ws, rank, local)
     if rank != 0:

@@ -154,9 +154,10 @@ las_status las_veff(las_ctx* ctx, const double* C_alpha, const double* w_alpha, 
  *   dG = directional derivative of dE/dC along dC                      (device [nao][nmo])
  *   Dg = d/dt g(C exp(tX)) at t = 0 = (C X)^T G + C^T dG - transpose   (device [nmo][nmo],
  *        NULL to skip; g = C^T dE/dC - transpose is the orbital-rotation gradient)
- * dE/dC is cubic in C, so dG is formed exactly (up to rounding) by a four-point rule over four
- * gradient evaluations along C + t dC (t = 0, tau, -tau, 2 tau).  The step is set from max|C| and
- * max|dC|, read back once (one stream synchronisation: not graph-capturable). */
+ * dG is the tangent of the evaluation chain (dE/dC = one-electron terms + sum_L H_L W(T_L), W
+ * linear in T): one more half transform b^L dC, one more full-transform product, two per-aux
+ * passes and two projections, next to one plain evaluation for G.  Asynchronous.  The first
+ * call allocates the tangent's scratch (about the evaluation's per-chunk workspace again). */
 las_status las_orbital_hvp(las_ctx* ctx, const double* C, const double* h, const double* dm1s,
                            const double* dm2, const double* X, double* dG, double* Dg);
 

@@ -79,8 +79,10 @@ struct las_ctx {
   int fnmo, fma;
   FragSplit* fsplit;
   double *vJ, *vK;   // scratch of las_veff (allocated by its first call)
-  double *hdC, *hCt, *hGt, *hG;   // scratch of las_orbital_hvp (dC, C + t dC, G(C + t dC), G(C))
-  unsigned long long* hmax;       // [2] |C| and |dC| maxima (bit patterns)
+  // scratch of las_orbital_hvp (allocated by its first call): dC = C X and G(C) [n][nmo]; the
+  // tangent chain's dC_occ, h dC_occ and projection [n][op], dH [Lc][op][n], X = H^T dC, dT and
+  // the two W matrices of the tangent [Lc][op][op]
+  double *hdC, *hG, *tCocc, *thC, *tOut, *tHt, *tX, *tdT, *tdW, *tWd;
   int* widx;          // [2*o + 2] columns of each weight sign and their counts (JK density)
   int wcount[2];      // host copy of those counts
   // timing: a ring of LAS_TIMING_RING evaluations x 6 stage marks, read without per-call syncs
@@ -124,8 +126,8 @@ static void free_all(las_ctx* x) {
     if (p) cudaFree(p);
   if (x->split) split_destroy(x->split);
   if (x->fsplit) frag_split_destroy(x->fsplit);
-  if (x->hmax) cudaFree(x->hmax);
-  for (double* q : {x->fH, x->fT, x->fpart, x->vJ, x->vK, x->hdC, x->hCt, x->hGt, x->hG})
+  for (double* q : {x->fH, x->fT, x->fpart, x->vJ, x->vK, x->hdC, x->hG, x->tCocc, x->thC,
+                    x->tOut, x->tHt, x->tX, x->tdT, x->tdW, x->tWd})
     if (q) cudaFree(q);
   if (x->ev) {
     for (int i = 0; i < LAS_TIMING_RING * LAS_MARKS; ++i)
@@ -669,59 +671,106 @@ extern "C" las_status las_veff(las_ctx* x, const double* Ca, const double* wa, i
 // ------------------------------------------------------------------------------------------
 // Orbital Hessian-vector product at fixed fragment RDMs
 // ------------------------------------------------------------------------------------------
-// dE/dC is a cubic polynomial in C (H = b C and the per-L matrices T = C^T b C, W(T) are of
-// degree 1, 2, 2; G = [one-electron terms, linear in C] + sum_L H_L W_L), so along the line
-// C + t dC the four-point rule
-//     dG = [6 G(tau) - 2 G(-tau) - G(2 tau) - 3 G(0)] / (6 tau),   G(t) = G(C + t dC),
-// which is exact for polynomials up to degree three, is the directional derivative without any
-// truncation error: only the rounding of the four evaluations enters, amplified by about
-// 2 (1 + 2 r)^3 / r with r = tau max|dC| / max|C| (tau is chosen for r = 1/4).  G(0) also
-// serves Dg.
+// dE/dC = [4 h C_c | 2 h C_a D | 0] + sum_L H_L W(T_L) with H_L = b^L C_occ, T_L = C_occ^T H_L
+// and W linear in T (the matrix the per-aux kernel builds), so its directional derivative along
+// dC is the tangent chain
+//     dG = [4 h dC_c | 2 h dC_a D | 0] + sum_L ( dH_L W(T_L) + H_L W(dT_L) ),
+//     dH_L = b^L dC_occ,   dT_L = X_L + X_L^T,   X_L = H_L^T dC_occ   (b^L symmetric):
+// one more half transform (dH), one more full-transform product (X), two per-aux passes and two
+// projections; in split precision W(T_L) is scaled by the row exponents of dH and W(dT_L) by those
+// of H, the operand each is projected against.  G(C) itself (for Dg) is one plain evaluation.
+static las_status tangent_grad(las_ctx* x, const double* h, const double* dm1s,
+                               const double* dm2, double* dG) {
+  const int n = x->n, op = x->op, nmo = x->nmo;
+  const bool split = x->prec == LAS_SPLIT_BF16;
+  las_status st;
+  launch_pack_cocc(x->hdC, n, nmo, x->o, op, x->tCocc, x->stream);   // dC_occ
+  if (split && (st = split_tangent_prepare(x->split, x->tCocc, x->stream, &x->bytes)) != LAS_OK)
+    return st;
+  if (split && (st = split_prepare_C(x->split, x->Cocc, x->stream)) != LAS_OK) return st;
+  for (int l0 = 0; l0 < x->X; l0 += x->Lc) {
+    const int nL = std::min(x->Lc, x->X - l0);
+    if (split) {
+      if ((st = split_half(x->split, l0, nL, op, x->Ht, x->stream)) != LAS_OK ||
+          (st = split_tangent_half(x->split, l0, nL, x->tHt, x->stream)) != LAS_OK ||
+          (st = split_full(x->split, nL, x->Ht, x->T, x->stream)) != LAS_OK ||
+          (st = split_tangent_full(x->split, nL, x->tHt, x->tX, x->stream)) != LAS_OK)
+        return st;
+    } else {
+      PackedSymA A{x->Bp, x->npair, l0};
+      StridedA Bc{x->Cocc, 0, op, 1}, Bd{x->tCocc, 0, op, 1};
+      gemm_f64(n, op, n, nL, 1, A, Bc, StridedC{x->Ht, (long)op * n, 1, n, 1.0, 0}, x->stream);
+      gemm_f64(n, op, n, nL, 1, A, Bd, StridedC{x->tHt, (long)op * n, 1, n, 1.0, 0}, x->stream);
+      StridedA Ah{x->Ht, (long)op * n, n, 1};
+      gemm_f64(op, op, n, nL, 1, Ah, Bc, StridedC{x->T, (long)op * op, op, 1, 1.0, 0}, x->stream);
+      gemm_f64(op, op, n, nL, 1, Ah, Bd, StridedC{x->tX, (long)op * op, op, 1, 1.0, 0},
+               x->stream);
+    }
+    launch_sym_add(x->tX, nL, op, x->tdT, x->stream);
+    // W(T) against dH and W(dT) against H (the per-aux outputs eps, vc, va are not needed)
+    const int* hexp = split ? split_hexp(x->split) : nullptr;
+    const int* dhexp = split ? split_tangent_dhexp(x->split) : nullptr;
+    launch_per_aux(x->T, nL, op, dm1s, dm2, x->fi, x->tWd, x->eps + l0, x->vc + l0, x->va + l0, 1,
+                   dhexp, x->status, x->stream);
+    launch_per_aux(x->tdT, nL, op, dm1s, dm2, x->fi, x->tdW, x->eps + l0, x->vc + l0, x->va + l0,
+                   1, hexp, x->status, x->stream);
+    if ((st = check_launch()) != LAS_OK) return st;
+    if (split) {
+      if ((st = split_tangent_project(x->split, nL, 0, x->tdW, x->tOut, l0 > 0, x->stream)) !=
+              LAS_OK ||
+          (st = split_tangent_project(x->split, nL, 1, x->tWd, x->tOut, 1, x->stream)) != LAS_OK)
+        return st;
+    } else {
+      const int ks = std::max(1, std::min(x->ksplit, (nL * op) / 64));
+      const double* Hs[2] = {x->Ht, x->tHt};
+      const double* Ws[2] = {x->tdW, x->tWd};
+      for (int k = 0; k < 2; ++k) {
+        StridedA A{Hs[k], 0, 1, n};
+        StridedA Bw{Ws[k], 0, op, 1};
+        StridedC Cp{x->part, (long)n * op, op, 1, 1.0, 0};
+        gemm_f64(n, op, nL * op, 1, ks, A, Bw, Cp, x->stream);
+        launch_reduce_partials(x->part, ks, (long)n * op, x->tOut, l0 > 0 || k > 0, x->stream);
+      }
+    }
+    if ((st = check_launch()) != LAS_OK) return st;
+  }
+  // h dC_occ
+  if (split) {
+    if ((st = split_one_electron_hc(x->split, h, x->hC, x->stream)) != LAS_OK ||
+        (st = split_tangent_one_electron(x->split, x->thC, x->stream)) != LAS_OK)
+      return st;
+  } else {
+    gemm_f64(n, op, n, 1, 1, StridedA{h, 0, n, 1}, StridedA{x->tCocc, 0, op, 1},
+             StridedC{x->thC, 0, op, 1, 1.0, 0}, x->stream);
+  }
+  launch_assemble_grad(x->tOut, x->thC, dm1s, x->fi, n, nmo, op, dG, x->stream);
+  return check_launch();
+}
+
 extern "C" las_status las_orbital_hvp(las_ctx* x, const double* C, const double* h,
                                       const double* dm1s, const double* dm2, const double* X,
                                       double* dG, double* Dg) {
   if (!x || !C || !h || !X || !dG) return LAS_ERR_ARG;
   if (x->a > 0 && (!dm1s || !dm2)) return LAS_ERR_ARG;
-  const int n = x->n, nmo = x->nmo;
+  const int n = x->n, nmo = x->nmo, op = x->op;
   const long nC = (long)n * nmo;
+  const size_t chunk = (size_t)x->Lc * op;
   las_status st = LAS_OK;
   if (!x->hdC) {
-    for (double** q : {&x->hdC, &x->hCt, &x->hGt, &x->hG})
-      if ((st = dalloc(x, (void**)q, sizeof(double) * nC)) != LAS_OK) return st;
-    if ((st = dalloc(x, (void**)&x->hmax, 2 * sizeof(unsigned long long))) != LAS_OK) return st;
+    const struct { double** p; size_t cnt; } bufs[] = {
+        {&x->hdC, (size_t)nC}, {&x->hG, (size_t)nC}, {&x->tCocc, (size_t)n * op},
+        {&x->thC, (size_t)n * op}, {&x->tOut, (size_t)n * op}, {&x->tHt, chunk * n},
+        {&x->tX, chunk * op}, {&x->tdT, chunk * op}, {&x->tdW, chunk * op},
+        {&x->tWd, chunk * op}};
+    for (const auto& b : bufs)
+      if ((st = dalloc(x, (void**)b.p, sizeof(double) * b.cnt)) != LAS_OK) return st;
   }
   // dC = C X
-  {
-    StridedA Ac{C, 0, nmo, 1};
-    StridedA Bx{X, 0, nmo, 1};
-    StridedC Cd{x->hdC, 0, nmo, 1, 1.0, 0};
-    gemm_f64(n, nmo, nmo, 1, 1, Ac, Bx, Cd, x->stream);
-  }
-  // step: tau max|dC| = max|C| / 4 (the maxima are read back once)
-  LAS_CUDA_TRY(cudaMemsetAsync(x->hmax, 0, 2 * sizeof(unsigned long long), x->stream));
-  launch_absmax_bits(C, nC, x->hmax, x->stream);
-  launch_absmax_bits(x->hdC, nC, x->hmax + 1, x->stream);
-  unsigned long long mx[2] = {0, 0};
-  LAS_CUDA_TRY(cudaMemcpyAsync(mx, x->hmax, sizeof(mx), cudaMemcpyDeviceToHost, x->stream));
-  LAS_CUDA_TRY(cudaStreamSynchronize(x->stream));
-  double cmax, dmax;
-  memcpy(&cmax, &mx[0], 8);
-  memcpy(&dmax, &mx[1], 8);
-  LAS_CUDA_TRY(cudaMemsetAsync(dG, 0, (size_t)nC * 8, x->stream));
+  gemm_f64(n, nmo, nmo, 1, 1, StridedA{C, 0, nmo, 1}, StridedA{X, 0, nmo, 1},
+           StridedC{x->hdC, 0, nmo, 1, 1.0, 0}, x->stream);
+  // G(C): C_occ, its digits and those of h stay in place for the tangent chain
   if ((st = evaluate(x, C, h, dm1s, dm2, x->dE, x->hG, nullptr)) != LAS_OK) return st;
-  if (dmax > 0.0) {
-    const double tau = 0.25 * cmax / dmax;
-    const double w[3] = {6.0, -2.0, -1.0};
-    const double t[3] = {1.0, -1.0, 2.0};
-    for (int k = 0; k < 3; ++k) {
-      LAS_CUDA_TRY(cudaMemcpyAsync(x->hCt, C, (size_t)nC * 8, cudaMemcpyDeviceToDevice,
-                                   x->stream));
-      launch_axpy(x->hCt, x->hdC, t[k] * tau, nC, x->stream);
-      if ((st = evaluate(x, x->hCt, h, dm1s, dm2, x->dE, x->hGt, nullptr)) != LAS_OK) return st;
-      launch_axpy(dG, x->hGt, w[k] / (6.0 * tau), nC, x->stream);
-    }
-    launch_axpy(dG, x->hG, -3.0 / (6.0 * tau), nC, x->stream);
-  }
+  if ((st = tangent_grad(x, h, dm1s, dm2, dG)) != LAS_OK) return st;
   if (Dg) {
     // Dg = (C X)^T G + C^T dG - transpose  (virtual columns of G and dG are zero)
     StridedA Ad{x->hdC, 0, 1, nmo};

@@ -91,6 +91,8 @@ void launch_per_aux(const double* T, int nL, int op, const double* dm1s, const d
 void launch_scale(double* p, long count, double a, cudaStream_t s);
 void launch_mirror_lower(double* K, int n, cudaStream_t s);
 void launch_axpy(double* y, const double* x, double a, long count, cudaStream_t s);
+// dT[L] = X[L] + X[L]^T for L < nL (op x op each)
+void launch_sym_add(const double* X, int nL, int op, double* dT, cudaStream_t s);
 // *out (atomic max, caller zeroes it) = max_i |a[i]| as the bit pattern of the double
 void launch_absmax_bits(const double* a, long count, unsigned long long* out, cudaStream_t s);
 // Columns of each sign of w (k_sign_split), then the packed factor of one sign

@@ -260,6 +260,16 @@ __global__ void k_mirror_lower(double* __restrict__ K, int n) {
   if (i < j) K[idx] = K[(long)j * n + i];
 }
 
+// dT[L][p][q] = X[L][p][q] + X[L][q][p]  (the symmetric tangent of T_L = C^T b^L C)
+__global__ void k_sym_add(const double* __restrict__ X, long nL, int op, double* __restrict__ dT) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const long per = (long)op * op;
+  if (i >= nL * per) return;
+  const long L = i / per, r = i - L * per;
+  const int p = (int)(r / op), q = (int)(r - (long)p * op);
+  dT[i] = X[i] + X[L * per + (long)q * op + p];
+}
+
 __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, double a, long count) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i < count) y[i] += a * x[i];
@@ -473,6 +483,13 @@ void launch_pack_weighted(const double* Cx, const double* w, const int* idx, int
 
 void launch_mirror_lower(double* K, int n, cudaStream_t s) {
   k_mirror_lower<<<nblk((long)n * n, 256), 256, 0, s>>>(K, n);
+  las_count_launch();
+}
+
+void launch_sym_add(const double* X, int nL, int op, double* dT, cudaStream_t s) {
+  const long count = (long)nL * op * op;
+  if (count <= 0) return;
+  k_sym_add<<<nblk(count, 256), 256, 0, s>>>(X, nL, op, dT);
   las_count_launch();
 }
 

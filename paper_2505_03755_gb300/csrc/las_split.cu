@@ -1161,11 +1161,19 @@ struct SplitState {
   int ksplit6;           // partial buffers allocated for this many K splits
   int ks;                // split-K factor of the projection GEMM (autotunable)
   int bn[SPLIT_NKIND];   // tile width of each product kind (autotunable): 64 or 96
+  // tangent (Hessian-vector) scratch, allocated by the first split_tangent_prepare: digit planes
+  // of dC_occ^T (rows p, K = nu) and of the chunk's dH (rows (L, p), K = mu)
+  Planes dCdig;
+  int* dCexp;
+  Planes dHdig;
+  int* dHexp;
+  void* tblob;
   int* status;
 };
 
 static void split_free(SplitState* s) {
   if (s->Mpblob) cudaFree(s->Mpblob);
+  if (s->tblob) cudaFree(s->tblob);
   void* ptrs[] = {s->Bdig.p, s->Bexp, s->Cdig.p, s->Cexp, s->Hdig.p, s->Hexp, s->HdigT.p,
                   s->Wdig.p, s->Wexp, s->part, s->mx, s->hdig.p, s->hexp, s->hcdig.p, s->hcexp};
   for (void* q : ptrs)
@@ -1282,6 +1290,89 @@ las_status split_prepare_C(SplitState* s, const double* Cocc, cudaStream_t st) {
   // rows p of C_occ^T (K = nu): element (p, nu) = Cocc[nu*op + p]
   RowsStrided acc{Cocc, 1, s->op, nullptr};
   return slice_rows(acc, s->Cdig, s->Cexp, st, nullptr, true);
+}
+
+// ------------------------------------------------------------------------------------------
+// Tangent of the evaluation along dC (the orbital Hessian-vector product): the same products
+// with dC_occ in place of C_occ where the chain rule puts it
+// ------------------------------------------------------------------------------------------
+las_status split_tangent_prepare(SplitState* s, const double* dCocc, cudaStream_t st,
+                                 size_t* bytes) {
+  if (!s->tblob) {
+    const long R = (long)s->Lc * s->op;
+    const size_t b0 = rup(planes_bytes(s->op, s->n), 256), b1 = rup((size_t)s->op * 4, 256);
+    const size_t b2 = rup(planes_bytes(R, s->n), 256), b3 = rup((size_t)R * 4, 256);
+    if (cudaMalloc(&s->tblob, b0 + b1 + b2 + b3) != cudaSuccess) {
+      s->tblob = nullptr;
+      las_record_cuda_error(cudaErrorMemoryAllocation, "cudaMalloc(tangent)", __FILE__, __LINE__);
+      return LAS_ERR_CUDA;
+    }
+    // padding rows are never written by the slicers: zero once
+    cudaError_t e = cudaMemsetAsync(s->tblob, 0, b0 + b1 + b2 + b3, st);
+    if (e != cudaSuccess) {
+      las_record_cuda_error(e, "cudaMemsetAsync(tangent)", __FILE__, __LINE__);
+      return LAS_ERR_CUDA;
+    }
+    uint8_t* w = (uint8_t*)s->tblob;
+    s->dCdig = make_planes(w, s->op, s->n);
+    s->dCexp = (int*)(w + b0);
+    s->dHdig = make_planes(w + b0 + b1, R, s->n);
+    s->dHexp = (int*)(w + b0 + b1 + b2);
+    *bytes += b0 + b1 + b2 + b3;
+  }
+  RowsStrided acc{dCocc, 1, s->op, nullptr};
+  return slice_rows(acc, s->dCdig, s->dCexp, st, nullptr, true);
+}
+
+// dH = b^L dC_occ for the chunk's aux rows (Ht layout [nL][op][n])
+las_status split_tangent_half(SplitState* s, int l0, int nL, double* dHt, cudaStream_t st) {
+  return ozaki_gemm(s->Bdig, (long)l0 * s->n, s->Bexp + (long)l0 * s->n, (long)nL * s->n,
+                    s->dCdig, 0, s->dCexp, s->op, s->n, 1, 1, dHt, 0, 0, s->n, s->op, s->status,
+                    st, 0, s->bn[SPLIT_HALF]);
+}
+
+// After split_full of the chunk: X[(L,p)][q] = sum_mu H_L(mu,p) dC(mu,q) (so that dT_L = X_L +
+// X_L^T), and the digits of dH (rows (L,p), K = mu) with their row exponents.
+las_status split_tangent_full(SplitState* s, int nL, const double* dHt, double* X,
+                              cudaStream_t st) {
+  const long R = (long)nL * s->op;
+  las_status rc = ozaki_gemm(s->Hdig, 0, s->Hexp, R, s->dCdig, 0, s->dCexp, s->op, s->n, 1, 0, X,
+                             s->op, 0, 0, 0, s->status, st, 0, s->bn[SPLIT_FULL]);
+  if (rc != LAS_OK) return rc;
+  k_slice_ht<<<(unsigned)((R + 15) / 16), 256, 0, st>>>(dHt, R, s->n, s->dHdig, s->dHexp);
+  las_count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "k_slice_ht launch", __FILE__, __LINE__);
+    return LAS_ERR_CUDA;
+  }
+  return LAS_OK;
+}
+
+const int* split_tangent_dhexp(SplitState* s) { return s->dHexp; }
+
+// Out (+)= sum_{(L,p)} A(mu,(L,p)) W((L,p),q): A = H (which = 0) or dH (which = 1), read
+// MN-major from its digit planes; Wt[q][(L,p)] holds W scaled by that operand's row exponents.
+las_status split_tangent_project(SplitState* s, int nL, int which, const double* Wt, double* Out,
+                                 int accumulate, cudaStream_t st) {
+  const long R = (long)nL * s->op;
+  Planes W = s->Wdig;
+  W.K = R;
+  las_status rc = slice_rows(RowsStrided{Wt, R, 1, nullptr}, W, s->Wexp, st, s->mx, true);
+  if (rc != LAS_OK) return rc;
+  const int ks = (int)std::max(1L, std::min((long)s->ks, (R + 32 * 64 - 1) / (32 * 64)));
+  rc = ozaki_gemm(which ? s->dHdig : s->Hdig, 0, nullptr, s->n, W, 0, s->Wexp, s->op, R, ks, 0,
+                  s->part, s->op, (long)s->n * s->op, 0, 0, s->status, st, 0,
+                  s->bn[SPLIT_PROJECT], 1);
+  if (rc != LAS_OK) return rc;
+  launch_reduce_partials(s->part, ks, (long)s->n * s->op, Out, accumulate, st);
+  return LAS_OK;
+}
+
+// hdC = h dC_occ (the digits of h from split_one_electron_hc of the same h)
+las_status split_tangent_one_electron(SplitState* s, double* hdC, cudaStream_t st) {
+  return ozaki_gemm(s->hdig, 0, s->hexp, s->n, s->dCdig, 0, s->dCexp, s->op, s->n, 1, 0, hdC,
+                    s->op, 0, 0, 0, s->status, st, 0, s->bn[SPLIT_ONE_ELECTRON]);
 }
 
 las_status split_lpu(SplitState* s, int nL, const double* Ht, int c, int a, const double* C,

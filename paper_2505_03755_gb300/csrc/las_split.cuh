@@ -85,3 +85,19 @@ las_status frag_split_chunk(SplitState* s, FragSplit* f, int l0, int nL, double*
 // the first call and their size is added to *bytes.
 las_status split_lpu(SplitState* s, int nL, const double* Ht, int c, int a, const double* C,
                      int nmo, int p0, int np, double* Lpu, cudaStream_t st, size_t* bytes);
+
+// Tangent of the evaluation along dC (orbital Hessian-vector product), split precision.
+// split_tangent_prepare slices dC_occ (and allocates the tangent scratch on its first call,
+// adding its size to *bytes); per chunk: split_tangent_half (dH = b dC_occ), then, after
+// split_full of H, split_tangent_full (X = H^T dC and the digits of dH), and
+// split_tangent_project for each of the two projection terms; split_tangent_one_electron gives
+// h dC_occ (after split_one_electron of the same h).
+las_status split_tangent_prepare(SplitState* s, const double* dCocc, cudaStream_t st,
+                                 size_t* bytes);
+las_status split_tangent_half(SplitState* s, int l0, int nL, double* dHt, cudaStream_t st);
+las_status split_tangent_full(SplitState* s, int nL, const double* dHt, double* X,
+                              cudaStream_t st);
+const int* split_tangent_dhexp(SplitState* s);
+las_status split_tangent_project(SplitState* s, int nL, int which, const double* Wt, double* Out,
+                                 int accumulate, cudaStream_t st);
+las_status split_tangent_one_electron(SplitState* s, double* hdC, cudaStream_t st);
