@@ -6,6 +6,29 @@
 
 namespace lasdf {
 
+// Deterministic block sums of K doubles per thread: warp butterflies (lane 0's order is fixed),
+// then the warp partials in warp order; every thread returns the K totals.  red: NT/32*K doubles.
+template <int NT, int K>
+__device__ void block_sums(double (&v)[K], double* red) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[w * K + k] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) t += red[i * K + k];
+    v[k] = t;
+  }
+  __syncthreads();
+}
+
 // Deterministic block reduction of one double per thread (fixed tree order).
 template <int NT>
 __device__ double block_sum(double v, double* red) {
@@ -91,9 +114,9 @@ k_per_aux(const double* __restrict__ T, int nL, int op, const double* __restrict
   }
   double pva = 0.0;
   for (int i = tid; i < a * a; i += 256) pva += Ds[i] * Taa[i];
-  const double vc = 2.0 * block_sum<256>(pvc, red);
-  const double fro = block_sum<256>(pcore, red);
-  const double va = block_sum<256>(pva, red);
+  double r3[3] = {pvc, pcore, pva};
+  block_sums<256, 3>(r3, red);
+  const double vc = 2.0 * r3[0], fro = r3[1], va = r3[2];
   if (tid < fi.nfrag) {
     int K = tid, o0 = fi.off[K], m = fi.off[K + 1] - o0;
     double s = 0.0;
@@ -195,8 +218,9 @@ k_per_aux(const double* __restrict__ T, int nL, int op, const double* __restrict
   }
   double pe = 0.0;
   for (int i = tid; i < a * a; i += 256) pe += Taa[i] * Y[i];
-  const double zt = block_sum<256>(pz, red);
-  const double ty = block_sum<256>(pe, red);
+  double r2[2] = {pz, pe};
+  block_sums<256, 2>(r2, red);
+  const double zt = r2[0], ty = r2[1];
   if (tid == 0) {
     eps[Lb] = 0.5 * vc * vc - fro + vc * va - zt + 0.5 * ty;
     vcv[Lb] = vc;
