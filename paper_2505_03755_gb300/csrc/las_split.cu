@@ -1412,12 +1412,27 @@ las_status split_lpu(SplitState* s, int nL, const double* Ht, int c, int a, cons
   return rc;
 }
 
+// When the half transform runs in 96-column tiles and the columns beyond the last whole tile
+// number at most 64 (the JK call's 150 core columns: 96 + 54), those columns form a second product
+// of 64-column tiles: 160 columns computed instead of 192, and a 64-column stage costs about three
+// quarters of a 96-column one.  Not while products are recorded for a grouped launch, which would
+// then mix tile widths.
 las_status split_half(SplitState* s, int l0, int nL, int oc, double* Ht, cudaStream_t st) {
   const long rows = (long)nL * s->n;
   if (oc < 1 || oc > s->op) return LAS_ERR_INTERNAL;
+  const int bn = s->bn[SPLIT_HALF];
+  const int whole = oc / 96 * 96, rest = oc - whole;
+  if (bn == 96 && whole > 0 && rest > 0 && rest <= 64 && !g_record) {
+    las_status rc = ozaki_gemm(s->Bdig, (long)l0 * s->n, s->Bexp + (long)l0 * s->n, rows,
+                               s->Cdig, 0, s->Cexp, whole, s->n, 1, 1, Ht, 0, 0, s->n, oc,
+                               s->status, st, 0, 96);
+    if (rc != LAS_OK) return rc;
+    return ozaki_gemm(s->Bdig, (long)l0 * s->n, s->Bexp + (long)l0 * s->n, rows, s->Cdig, whole,
+                      s->Cexp + whole, rest, s->n, 1, 1, Ht + (size_t)whole * s->n, 0, 0, s->n,
+                      oc, s->status, st, 0, 64);
+  }
   return ozaki_gemm(s->Bdig, (long)l0 * s->n, s->Bexp + (long)l0 * s->n, rows, s->Cdig, 0,
-                    s->Cexp, oc, s->n, 1, 1, Ht, 0, 0, s->n, oc, s->status, st, 0,
-                    s->bn[SPLIT_HALF]);
+                    s->Cexp, oc, s->n, 1, 1, Ht, 0, 0, s->n, oc, s->status, st, 0, bn);
 }
 
 las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaStream_t st) {
