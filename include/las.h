@@ -69,7 +69,8 @@ typedef struct {
 } las_dims;
 
 /* Create a context over the packed Cholesky vectors B_packed (device, naux*nao(nao+1)/2
- * doubles).  In LAS_FP64 mode the context keeps a reference to B_packed, which must stay valid
+ * doubles), the factors b^P of Eq. cholesky in the packed lower-triangle storage of section
+ * "Calculation of effective potentials".  In LAS_FP64 mode the context keeps a reference to B_packed, which must stay valid
  * and unchanged until las_destroy.  In LAS_SPLIT_BF16 mode it builds, once, the digit planes of
  * B (owned by the context); afterwards B_packed is read only by the JK calls (las_df_jk,
  * las_df_jk_density, las_veff: the Coulomb matrix is accumulated over the packed triangle), so
@@ -161,7 +162,11 @@ las_status las_veff(las_ctx* ctx, const double* C_alpha, const double* w_alpha, 
 las_status las_orbital_hvp(las_ctx* ctx, const double* C, const double* h, const double* dm1s,
                            const double* dm2, const double* X, double* dG, double* Dg);
 
-/* LAS energy.  h: device [nao][nao] one-electron Hamiltonian (symmetric).
+/* LAS energy E_LAS = <LAS|H|LAS> of the product state of Eq. las_wfn (section "LASSCF
+ * algorithm"; no constant term, as with Eq. h_emb), from the core and active densities: the
+ * Coulomb and exchange parts of Eqs. J_1-K_2 and the active integrals of Eq. ppaa, both formed
+ * per auxiliary index from b^L C_occ and never stored whole.
+ * h: device [nao][nao] one-electron Hamiltonian (symmetric).
  * dm1s: device, per fragment K the spin-separated 1-RDM [2][m_K][m_K] (alpha, beta),
  *       concatenated over fragments.
  * dm2:  device, per fragment K the spin-summed 2-RDM [m_K]^4 in chemists' order,
@@ -170,7 +175,8 @@ las_status las_orbital_hvp(las_ctx* ctx, const double* C, const double* h, const
 las_status las_energy(las_ctx* ctx, const double* C, const double* h, const double* dm1s,
                       const double* dm2, double* E);
 
-/* LAS energy and its derivative with respect to the MO coefficients:
+/* LAS energy and its derivative with respect to the MO coefficients (the gradient whose
+ * vanishing is Eq. MO_conv):
  *   dEdC: device [nao][nmo], dE/dC[mu][p] (zero in the virtual columns);
  *   gorb: device [nmo][nmo] or NULL, the antisymmetric orbital-rotation gradient
  *         g = C^T dEdC - (C^T dEdC)^T, so that d/de E(C exp(e X))|_0 = sum_pq g[p][q] X[p][q] / 2

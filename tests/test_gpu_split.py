@@ -57,6 +57,22 @@ def test_split_gemm_digit_groups_bit_exact(wa, wb):
     assert np.array_equal(_gemm(A, B), A @ B)
 
 
+def test_split_gemm_large_exact_sums_bit_exact():
+    """Digit products of one sign: the exact-group partial sums of a 256-long chunk come close to
+    their 2^24 bound (group 1: 2 * 127 * 72 * 256 = 4.7e6 in units of 2^-8), next to rows of
+    mixed-sign digits (rows 64..127) in the same tiles.  Every entry has two digits, so the
+    product is exact in FP64 and the split result must equal it bit for bit."""
+    rng = np.random.default_rng(11)
+    a = 127 * 2.0 ** -7 - 72 * 2.0 ** -15          # digits d_0 = 127, d_1 = -72
+    A = np.full((256, 1024), a)
+    A[64:128] = _digit_matrix(64, 1024, [0, 1], rng)
+    A[192:] = -a
+    B = np.full((1024, 160), a)
+    B[:, 100:] = _digit_matrix(60, 1024, [0, 1], rng).T
+    C = _gemm(A, B)
+    assert np.array_equal(C, A @ B)
+
+
 @pytest.mark.parametrize("M,K,N", [(1, 5, 3), (128, 32, 96), (257, 1111, 190), (130, 700, 16)])
 def test_split_gemm_random_fp64(M, K, N):
     rng = np.random.default_rng(M + K + N)
