@@ -263,7 +263,8 @@ def run_ours(args, ws, rank, local):
     work = algorithmic_work(s.nao, s.naux, s.ncore, s.nactive)
     peaks = measured_peaks()
 
-    precs = ["split", "fp64"] if args.precision == "both" else [args.precision]
+    # "split_packed": the split mode over packed-triangle digit planes of B, timed as a side mode
+    precs = ["split", "fp64", "split_packed"] if args.precision == "both" else [args.precision]
     results = {}
     # the FP64 roofline's denominator, measured on this GPU in this run (register-resident
     # DMMA and DFMA loops over all SMs)
@@ -273,8 +274,9 @@ def run_ours(args, ws, rank, local):
         dmma, dfma = probe_fp64()
         fp64_peak = {"dmma_tflops": dmma, "dfma_tflops": dfma}
     for prec in precs:
-        steps = args.steps if prec == precs[0] else max(1, min(args.steps, args.fp64_steps))
-        warm = args.warmup if prec == precs[0] else max(1, min(args.warmup, args.fp64_warmup))
+        split = prec in SPLIT_MODES
+        steps = args.steps if split else max(1, min(args.steps, args.fp64_steps))
+        warm = args.warmup if split else max(1, min(args.warmup, args.fp64_warmup))
         try:
             las = LasDF(Bd, s.nao, s.naux, s.nmo, s.ncore, s.nact, precision=prec, stream=stream)
         except Exception as e:  # a precision mode the library does not provide
@@ -284,8 +286,12 @@ def run_ours(args, ws, rank, local):
         G = torch.empty((s.nao, s.nmo), dtype=torch.float64, device=dev)
         tiles = None
         with torch.cuda.stream(stream):
-            if prec == "split":   # the library's autotuner: tile widths and projection split-K
+            # the library's autotuner: tile widths and projection split-K (skipped in profiling
+            # mode, so that every evaluation launches the same kernels in the same order; the
+            # 96-column tiles it keeps for the Nao=1200 half transform are the default)
+            if split and not args.profile_naux:
                 las.autotune(C, h, d1, d2)
+            if split:
                 tiles = las.tiles()
             for _ in range(warm):
                 las.energy_grad(C, h, d1, d2, E=E, G=G)
@@ -347,7 +353,7 @@ def run_ours(args, ws, rank, local):
         jk_ms = e0.elapsed_time(e1) / jsteps
         # effective potentials of the LAS state (Eq. v_emb): both spin densities, rank c + a
         veff_ms = None
-        if prec == "split":
+        if split:
             fac = spin_density_factors(s)
             Cs = [torch.from_numpy(np.ascontiguousarray(f[0])).to(dev) for f in fac]
             Ws = [torch.from_numpy(f[1]).to(dev) for f in fac]
@@ -360,7 +366,7 @@ def run_ours(args, ws, rank, local):
             veff_ms = e0.elapsed_time(e1)
         # AO2MO transforms of the active orbitals over all MOs (Eqs. ao2mo_1, ao2mo_2)
         with torch.cuda.stream(stream):
-            if prec == "split":
+            if split:
                 las.df_transform(C, 0, s.nmo)
             e0.record(stream)
             lmu, lpu = las.df_transform(C, 0, s.nmo)
@@ -370,7 +376,7 @@ def run_ours(args, ws, rank, local):
         del lmu, lpu
                 # orbital Hessian-vector product along a seeded antisymmetric rotation (split mode)
         hvp_ms = None
-        if prec == "split":
+        if split:
             rng = np.random.default_rng(rank_seed(rank))
             Xr = rng.standard_normal((s.nmo, s.nmo))
             Xd = torch.from_numpy((Xr - Xr.T) / np.sqrt(2.0)).to(dev)
@@ -381,8 +387,10 @@ def run_ours(args, ws, rank, local):
                 e1.record(stream)
                 e1.synchronize()
             hvp_ms = e0.elapsed_time(e1)
+        dev_gb = las.device_bytes() / 1e9
         las.close()
         results[prec] = dict(G=G_keep, ms_per_step=ms / steps, steps=steps, warmup=warm,
+                             device_gb=dev_gb,
                              evals_per_s=weak_scaling_rate(ws, steps, ms / 1e3),
                              stage_ms=stage_ms, E=E_val,
                              e2e_evals_per_s=weak_scaling_rate(ws, steps, t_e2e), e2e_E=e2e_E,
@@ -395,25 +403,32 @@ def run_ours(args, ws, rank, local):
 
 
 NDIG_PRODUCTS = 21     # digit products of the split-precision GEMM (6 digits, s + t <= 5)
-# DRAM bytes per (L, mu) row of the half-transform kernel (K = Nao = 1200, 176 columns), from one
-# ncu capture of the same launch on the first 200 auxiliary functions (200 x 1200 rows;
-# profiles/k_ozaki_half_transform_nao1200_naux200.md), scaled to a full launch by the rows it
-# processes (the traffic is proportional to the rows: digits of B read once, H written once).
-S1_TRAFFIC_PER_ROW = (3.534248e9 + 0.386613e9) / (200 * 1200)
+SPLIT_MODES = ("split", "split_packed")
+# DRAM bytes per (L, mu) row of the half transform, from one ncu capture of its launches on the
+# first 200 auxiliary functions of the Nao=1200 workload (200 x 1200 rows), scaled to a full
+# evaluation by the rows processed (the traffic is proportional to the rows: digits of B read
+# once, H written once).  "split_packed" sums the two launches of that layout (the whole 128-row
+# blocks and the ragged rows).
+S1_TRAFFIC_PER_ROW = {"split": (3525893376 + 378322688) / (200 * 1200),
+                      "split_packed": (2033419008 + 354386688 + 141700352 + 989952) / (200 * 1200)}
 
 
 def roofline_for(prec, r, work, peaks, s):
     if "stage_ms" not in r or not r["stage_ms"]:
         return None
     t_s1 = r["stage_ms"][0] / 1e3
-    if prec == "split":
+    if prec in SPLIT_MODES:
         flops = NDIG_PRODUCTS * work["s1"]
         achieved = flops / t_s1 / 1e12
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
-        traffic = S1_TRAFFIC_PER_ROW * s.naux * s.nao if S1_TRAFFIC_PER_ROW else None
+        per_row = S1_TRAFFIC_PER_ROW[prec]
+        traffic = per_row * s.naux * s.nao if per_row else None
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_ozaki (half transform, tcgen05 BF16 digit products)",
+                "kernel": "k_ozaki (half transform, tcgen05 BF16 digit products)"
+                if prec == "split" else
+                "k_ozaki (half transform over packed-triangle digit planes of B: whole 128-row "
+                "blocks, then the ragged rows)",
                 "peak_source": "bf16_tflops_sustained of MEASURED_PEAKS.json (of measured)"
                 if peaks.get("bf16_tflops_sustained") else "of fallback (1.7 PFLOP/s sustained)",
                 "algorithmic_flops": flops}
@@ -735,7 +750,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="both", choices=["both", "split", "fp64"])
+    ap.add_argument("--precision", default="both",
+                    choices=["both", "split", "fp64", "split_packed"])
     ap.add_argument("--partition", default=None, choices=["aux", "systems"],
                     help="'aux' (the default for N > 1) splits the one Nao=1200 system along the "
                          "auxiliary index (one all-reduce per evaluation, strong scaling; with "
@@ -859,7 +875,12 @@ def main():
         accuracy = {"abs_dE_Eh": abs(res["split"]["E"] - res["fp64"]["E"]),
                     "max_abs_dG": float(np.abs(res["split"]["G"] - res["fp64"]["G"]).max()),
                     "max_abs_G": float(np.abs(res["fp64"]["G"]).max())}
-    primary = "split" if ("split" in res and "error" not in res["split"]) else "fp64"
+        if "split_packed" in res and "error" not in res["split_packed"]:
+            accuracy["split_packed"] = {
+                "abs_dE_Eh": abs(res["split_packed"]["E"] - res["fp64"]["E"]),
+                "max_abs_dG": float(np.abs(res["split_packed"]["G"] - res["fp64"]["G"]).max())}
+    primary = next(k for k in ("split", "split_packed", "fp64")
+                   if k in res and "error" not in res[k])
     r = res[primary]
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
@@ -881,7 +902,8 @@ def main():
                     if v.get("jk_ms") else None,
                     "veff_ms": v.get("veff_ms"), "orbital_hvp_ms": v.get("hvp_ms"),
                     "df_transform_ms": v.get("dft_ms"),
-                    "tile_widths_s1_s2_proj_one": v.get("tiles")}
+                    "tile_widths_s1_s2_proj_one": v.get("tiles"),
+                    "device_gb": v.get("device_gb")}
     line = {"metric": METRIC, "value": r["evals_per_s"], "unit": "evals/s", "n_gpus": ws,
             "steps": r["steps"], "warmup": r["warmup"], "ms_per_step": r["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -54,9 +54,22 @@ typedef enum {
 
 typedef enum {
   LAS_FP64 = 0,       /* all contractions in native FP64 (DMMA) */
-  LAS_SPLIT_BF16 = 1  /* bulk contractions as split-precision (BF16 digit) GEMMs on tcgen05
+  LAS_SPLIT_BF16 = 1, /* bulk contractions as split-precision (BF16 digit) GEMMs on tcgen05
                          with exact FP32 partial sums recombined in integer arithmetic;
-                         reductions, traces and gradient assembly stay in FP64 */
+                         reductions, traces and gradient assembly stay in FP64.  The digit
+                         planes of B hold the full rows of every b^L, each row scaled by its
+                         own power of two */
+  LAS_SPLIT_BF16_PACKED = 2
+                      /* LAS_SPLIT_BF16 with the digit planes of B in packed-triangle form
+                         (section "Calculation of effective potentials": only the lower
+                         triangle of each b^L is stored): 128 x 128 tiles of the lower triangle,
+                         the diagonal tiles whole, the rows past the last whole 128-row block
+                         whole; the half transform reads a stored tile as it is for its own row
+                         block and transposed for its column block.  One power of two per b^L
+                         (a stored element serves two rows), so about one bit less precision in
+                         the half transform; about 0.55 of the digit bytes (46 GB instead of
+                         83 GB at Nao = 1200, Naux = 4800).  Every call behaves as in
+                         LAS_SPLIT_BF16. */
 } las_precision;
 
 typedef struct {

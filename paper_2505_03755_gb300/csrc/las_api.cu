@@ -149,7 +149,12 @@ extern "C" las_status las_create(las_ctx** out, const las_dims* d, const double*
   *out = nullptr;
   if (d->nao <= 0 || d->naux <= 0 || d->nmo <= 0 || d->ncore < 0 || d->nfrag < 0) return LAS_ERR_ARG;
   if (d->nfrag > LAS_MAX_FRAG || (d->nfrag > 0 && !d->nact)) return LAS_ERR_ARG;
-  if (prec != LAS_FP64 && prec != LAS_SPLIT_BF16) return LAS_ERR_ARG;
+  if (prec != LAS_FP64 && prec != LAS_SPLIT_BF16 && prec != LAS_SPLIT_BF16_PACKED)
+    return LAS_ERR_ARG;
+  // the packed-triangle digit layout is a variant of the split mode: the context runs as
+  // LAS_SPLIT_BF16 everywhere else
+  const int packed = prec == LAS_SPLIT_BF16_PACKED;
+  if (packed) prec = LAS_SPLIT_BF16;
   int a = 0;
   for (int k = 0; k < d->nfrag; ++k) {
     if (d->nact[k] < 1) return LAS_ERR_ARG;
@@ -246,8 +251,8 @@ extern "C" las_status las_create(las_ctx** out, const las_dims* d, const double*
     st = per_aux_prepare(a);
   }
   if (st == LAS_OK && prec == LAS_SPLIT_BF16) {
-    st = split_create(&x->split, x->n, x->X, x->op, x->Lc, B_packed, x->status, x->stream,
-                      &x->bytes);
+    st = split_create(&x->split, x->n, x->X, x->op, x->Lc, B_packed, packed, x->status,
+                      x->stream, &x->bytes);
   }
   if (st == LAS_OK) {
     cudaError_t e = cudaStreamSynchronize(x->stream);
@@ -971,9 +976,11 @@ static int batch_rounds(int nsys, las_ctx* const* ctxs) {
   return rounds;
 }
 
-// Device bytes reserved per grouped launch: at most two products per problem.
+// Device bytes reserved per grouped launch: at most three products per problem (the half
+// transform's two -- full row blocks of the packed triangle and ragged rows -- and h C_occ).
+constexpr int kMaxGroupedPerProblem = 3;
 static size_t batch_slot_bytes(int nsys) {
-  return (ozgroup_bytes(2 * (size_t)nsys) + 255) / 256 * 256;
+  return (ozgroup_bytes(kMaxGroupedPerProblem * (size_t)nsys) + 255) / 256 * 256;
 }
 
 static las_status capture_grouped(const BatchPlan& P, las_ctx* const* ctxs,
@@ -1004,6 +1011,7 @@ static las_status capture_grouped(const BatchPlan& P, las_ctx* const* ctxs,
     if (record) ozgroup_record(nullptr);
     if (r != LAS_OK) return r;
     if ((r = plan_join(P)) != LAS_OK) return r;
+    if (record && ozgroup_bytes(ozgroup_count(g)) > slot) return LAS_ERR_INTERNAL;
     if (record && (r = ozgroup_launch(g, (uint8_t*)dev + (groups->size() - 1) * slot, P.cs)) !=
                       LAS_OK)
       return r;

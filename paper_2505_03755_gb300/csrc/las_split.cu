@@ -103,6 +103,38 @@ static inline Planes make_planes(void* p, long R, long K) {
   return P;
 }
 
+// The Cholesky vectors as digit planes in packed-triangle form.  The first n1 = 128 nb1 rows of
+// every b^L lie in full 128-row blocks, of which only the lower tiles (I >= J) are stored (the
+// diagonal tiles whole): T = nb1 (nb1 + 1) / 2 tiles per L, tile (I, J) of L at index
+// L T + I (I + 1) / 2 + J, each as 8 K blocks of 128 rows x 16 (the Planes layout with 128 rows
+// and 8 X T K blocks).  The half transform reads a tile as it is stored for the rows of block I
+// and MN-major (transposed) for the rows of block J.  The r = n - n1 ragged rows mu >= n1 of each
+// b^L are stored whole (rows (L, mu - n1), K = nu); they are read as they are for their own rows
+// and MN-major for the columns nu >= n1 of the full blocks.  One exponent per L (max |b^L| <
+// 2^e(L)), so that a stored element has the same scale for both rows that use it.
+struct BPacked {
+  int n, X, nb1, T, r, n1;
+  Planes tiles;       // R = Rpad = 128, nkb = 8 X T
+  Planes rag;         // rows (L, j), j < r, of all X r; K = n
+  int* exp;           // [X]
+  unsigned long long* mx;   // [X] max |b^L| as ordered bit patterns (set-up scratch)
+};
+
+static inline BPacked bpacked_geometry(int n, int X) {
+  BPacked b;
+  memset(&b, 0, sizeof(b));
+  b.n = n;
+  b.X = X;
+  b.nb1 = n / 128;
+  b.T = b.nb1 * (b.nb1 + 1) / 2;
+  b.n1 = 128 * b.nb1;
+  b.r = n - b.n1;
+  return b;
+}
+static inline size_t bpacked_tile_bytes(const BPacked& b) {
+  return (size_t)NDIG * 8 * (size_t)b.X * b.T * 128 * BK * 2;
+}
+
 struct OzParams {
   int M, N;                // output rows / columns
   int a_rpad, b_rpad;      // padded rows of the A / B plane layouts
@@ -121,6 +153,16 @@ struct OzParams {
   int sh;                  // fractional bits kept when merging the tail
   int bn;                  // tile width: 64 or 96 columns
   int a_mn;                // A read MN-major: rows of the stored planes are K, their K is M
+  // A = the Cholesky vectors in packed-triangle digit form (a_pack != 0; see BPacked): the
+  // product's row tiles are the full 128-row blocks R of each b^L (tile m = L * pk_nb1 + R of the
+  // chunk), and each 16-wide K block is read from the stored lower tile (R, J) as is (J <= R),
+  // from the stored tile (J, R) MN-major (R < J < pk_nb1), or from the ragged rows nu >= n1 of
+  // b^L MN-major (tensor maps tmA, tmA2 and tmA3)
+  int a_pack;
+  int pk_nb1, pk_T, pk_r;  // full row blocks per L, stored tiles per L, ragged rows per L
+  int pk_L0;               // first auxiliary index of the chunk
+  int ht_rows, ht_mu0;     // mode 1: rows of the product per L, and mu of its first row
+  int ea_perL;             // the row exponents are per auxiliary index: ea[L], not ea[row]
   int* status;
 };
 
@@ -167,7 +209,7 @@ __device__ __forceinline__ void tile_coords(const OzParams& p, long t, int& m0, 
 // One product of a grouped launch: its tensor maps, parameters and first tile in the launch's
 // tile order (problems are concatenated; tile0 of problem g+1 = tile0 + tiles of problem g).
 struct OzProblem {   // aligned as its tensor maps
-  CUtensorMap tmA, tmB;
+  CUtensorMap tmA, tmB, tmA2, tmA3;   // tmA2, tmA3: packed-triangle A only
   OzParams p;
   long tile0;
 };
@@ -180,9 +222,12 @@ struct OzCursor {
   const OzParams* P = nullptr;
   const CUtensorMap* ma = nullptr;
   const CUtensorMap* mb = nullptr;
+  const CUtensorMap* ma2 = nullptr;
+  const CUtensorMap* ma3 = nullptr;
   int m0 = 0, n0 = 0, kb0 = 0, nkb = 0;
   __device__ __forceinline__ bool seek(long t, const OzParams& p1, const CUtensorMap* a1,
-                                       const CUtensorMap* b1, const OzProblem* probs,
+                                       const CUtensorMap* b1, const CUtensorMap* a2,
+                                       const CUtensorMap* a3, const OzProblem* probs,
                                        int nprob) {
     long tl = t;
     bool moved = P == nullptr;
@@ -194,11 +239,15 @@ struct OzCursor {
       P = &probs[g].p;
       ma = &probs[g].tmA;
       mb = &probs[g].tmB;
+      ma2 = &probs[g].tmA2;
+      ma3 = &probs[g].tmA3;
       tl = t - probs[g].tile0;
     } else {
       P = &p1;
       ma = a1;
       mb = b1;
+      ma2 = a2;
+      ma3 = a3;
     }
     tile_coords(*P, tl, m0, n0, kb0, nkb);
     return moved;
@@ -267,10 +316,13 @@ __device__ __forceinline__ void mma_exact(uint32_t tmem, uint32_t sa, uint32_t s
 // GROUPED: the launch walks the concatenated tiles of nprob products described in global
 // memory (probs); otherwise the one product of the kernel parameters.  FIXBN: the tile width of
 // every product of the launch as a compile-time constant (64 or 96), or 0 when products of both
-// widths share a grouped launch (each tile then reads its product's width).
-template <int BN, bool GROUPED, int FIXBN>
+// widths share a grouped launch (each tile then reads its product's width).  PACK: the launch
+// may hold products whose A is the packed-triangle form of the Cholesky vectors (a_pack); the
+// other instantiations leave that logic out of the issuing and loading threads entirely.
+template <int BN, bool GROUPED, int FIXBN, bool PACK>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+        const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmA3,
         const __grid_constant__ OzParams p1, const OzProblem* __restrict__ probs, int nprob,
         long ntiles) {
   using T = OzTile<BN>;
@@ -306,6 +358,10 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     if (!GROUPED) {
       sm100::tma_prefetch_desc(&tmA);
       sm100::tma_prefetch_desc(&tmB);
+      if (PACK && p1.a_pack) {
+        sm100::tma_prefetch_desc(&tmA2);
+        sm100::tma_prefetch_desc(&tmA3);
+      }
     }
   }
   if (warp == 1) {
@@ -323,11 +379,28 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     bool ok = true;
     OzCursor<GROUPED> cur;
     for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      if (cur.seek(t, p1, &tmA, &tmB, probs, nprob) && GROUPED) {
+      if (cur.seek(t, p1, &tmA, &tmB, &tmA2, &tmA3, probs, nprob) && GROUPED) {
         sm100::tma_prefetch_desc(cur.ma);
         sm100::tma_prefetch_desc(cur.mb);
+        if (PACK && cur.P->a_pack) {
+          sm100::tma_prefetch_desc(cur.ma2);
+          sm100::tma_prefetch_desc(cur.ma3);
+        }
       }
       const OzParams& p = *cur.P;
+      // packed-triangle A, per tile: its row block R of b^L (tile (L, R) of the chunk), the K
+      // block of stored tile (R, 0), the index of stored tile (R, R) less R (R + 1) / 2, and the
+      // ragged row of K block 0, so that each stage adds its K block kb = 8 J + kk only
+      int pk_R = 0;
+      long pk_row = 0, pk_col = 0, pk_rag = 0;
+      if (PACK && p.a_pack) {
+        const int mt = cur.m0 / BM, Lr = mt / p.pk_nb1;
+        pk_R = mt - Lr * p.pk_nb1;
+        const long Lg = (long)p.pk_L0 + Lr;
+        pk_row = (Lg * p.pk_T + pk_R * (pk_R + 1) / 2) * 8;
+        pk_col = Lg * p.pk_T + pk_R;
+        pk_rag = Lg * p.pk_r - 8L * p.pk_nb1 * BK;
+      }
       for (int i = 0; i < cur.nkb; ++i, ++gs) {
         const int st = (int)(gs % NSTAGE);
         if (gs >= NSTAGE && !sm100::mbar_wait(&empty[st], (uint32_t)((gs / NSTAGE) - 1) & 1,
@@ -338,10 +411,21 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
         uint8_t* sa = smem + st * T::STAGE_BYTES;
         sm100::mbar_arrive_expect_tx(&full[st], A_BYTES + NDIG * (FIXBN ? FIXBN : p.bn) * BK * 2);
         const int kb = cur.kb0 + i;
-        if (p.a_mn)   // rows of the stored planes are this product's K, their K blocks its M
+        if (PACK && p.a_pack) {   // K block kb = 8 J + kk lies in column block J of b^L
+          const int J = kb >> 3;
+          if (J <= pk_R)           // stored lower tile (R, J): rows mu, K = nu
+            sm100::tma_load_3d(sa, cur.ma, &full[st], 0, (int)((pk_row + kb) * BM), 0);
+          else if (J < p.pk_nb1)   // stored tile (J, R) read MN-major: its rows are this K
+            sm100::tma_load_4d(sa, cur.ma2, &full[st], 0, (kb & 7) * BK,
+                               (int)((pk_col + J * (J + 1) / 2) * 8), 0);
+          else                     // ragged rows nu >= n1 of b^L, MN-major
+            sm100::tma_load_4d(sa, cur.ma3, &full[st], 0, (int)(pk_rag + (long)kb * BK),
+                               pk_R * (BM / BK), 0);
+        } else if (p.a_mn) {   // rows of the stored planes are this product's K, their K blocks its M
           sm100::tma_load_4d(sa, cur.ma, &full[st], 0, p.a_row0 + kb * BK, cur.m0 / BK, 0);
-        else
+        } else {
           sm100::tma_load_3d(sa, cur.ma, &full[st], 0, kb * p.a_rpad + p.a_row0 + cur.m0, 0);
+        }
         sm100::tma_load_3d(sa + A_BYTES, cur.mb, &full[st], 0,
                            kb * p.b_rpad + p.b_row0 + cur.n0, 0);
       }
@@ -359,11 +443,14 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     bool ok = true, need_acce = false;
     OzCursor<GROUPED> cur;
     for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      cur.seek(t, p1, &tmA, &tmB, probs, nprob);
+      cur.seek(t, p1, &tmA, &tmB, &tmA2, &tmA3, probs, nprob);
       const OzParams& p = *cur.P;
       const int nkb = cur.nkb;
       const int bn = FIXBN ? FIXBN : p.bn;
-      const bool amn = p.a_mn != 0;
+      const bool amn_tile = p.a_mn != 0;
+      // packed-triangle A: K blocks of column blocks J > R (above the diagonal) are read MN-major
+      const bool pack = PACK && p.a_pack != 0;
+      const int kb_mn = pack ? 8 * ((cur.m0 / BM) % p.pk_nb1 + 1) : 0;
       // the tail accumulators of the previous tile must have been read out
       if (tcount > 0) {
         if (!sm100::mbar_wait(accT, (uint32_t)(tcount - 1) & 1, abort_flag, p.status,
@@ -386,6 +473,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
         {
           const uint32_t sa = sm100::smem_u32(smem + st * T::STAGE_BYTES);
           const uint32_t sb = sa + A_BYTES;
+          const bool amn = PACK ? (pack ? (cur.kb0 + i >= kb_mn) : amn_tile) : amn_tile;
           // tail: the 11 products of groups 4 and 5 into the one tail accumulator
           if (bn == 64) mma_tail<64>(tmem + T::TAIL_COL, sa, sb, i == 0, amn);
           else mma_tail<96>(tmem + T::TAIL_COL, sa, sb, i == 0, amn);
@@ -423,6 +511,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
           const bool first_in_chunk = (i2 % CHUNK) == 0;
           const uint32_t sa = sm100::smem_u32(smem + st2 * T::STAGE_BYTES);
           const uint32_t sb = sa + A_BYTES;
+          const bool amn = PACK ? (pack ? (cur.kb0 + i2 >= kb_mn) : amn_tile) : amn_tile;
           if (bn == 64) mma_exact<64>(tmem, sa, sb, first_in_chunk, amn);
           else mma_exact<96>(tmem, sa, sb, first_in_chunk, amn);
           sm100::mma_commit(&empty[st2]);
@@ -448,7 +537,7 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     bool ok = true;
     OzCursor<GROUPED> cur;
     for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      cur.seek(t, p1, &tmA, &tmB, probs, nprob);
+      cur.seek(t, p1, &tmA, &tmB, &tmA2, &tmA3, probs, nprob);
       const OzParams& p = *cur.P;
       const int m0 = cur.m0, n0 = cur.n0, kb0 = cur.kb0, nkb = cur.nkb;
       const int bn = FIXBN ? FIXBN : p.bn;
@@ -518,11 +607,20 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
       if (!ok) break;
       // FP64 results (overlaps the next tile's MMAs)
       const int row = m0 + lq * 32 + lane;
-      const int ea = (p.ea && row < p.M) ? p.ea[row] : 0;
       long L = 0, mu = 0;
-      if (p.mode == 1) {
-        L = row / p.ht_n;
-        mu = row - L * p.ht_n;
+      int ea;
+      if constexpr (PACK) {
+        if (p.mode == 1) {   // row (L, mu) of the Ht layout
+          L = row / p.ht_rows;
+          mu = p.ht_mu0 + (row - L * p.ht_rows);
+        }
+        ea = (p.ea && row < p.M) ? p.ea[p.ea_perL ? L : row] : 0;
+      } else {
+        ea = (p.ea && row < p.M) ? p.ea[row] : 0;
+        if (p.mode == 1) {
+          L = row / p.ht_n;
+          mu = row - L * p.ht_n;
+        }
       }
       const int z = kb0 / p.kb_per_split;
 #pragma unroll
@@ -721,6 +819,83 @@ k_digits_long(Acc acc, Planes P, long rows, long kbc, const unsigned long long* 
   for (int s = 0; s < NDIG; ++s) P.p[P.idx(s, r, k)] = d[s];
 }
 
+// Packed-triangle digit planes of B (see BPacked).  Pass 1: max |b^L| over the packed triangle
+// of each L (one block per L) and its exponent.
+__global__ void __launch_bounds__(256)
+k_bpacked_max(const double* __restrict__ Bp, long npair, unsigned long long* __restrict__ mx,
+              int* __restrict__ ex) {
+  __shared__ unsigned long long red[8];
+  const long L = blockIdx.x;
+  const double* b = Bp + L * npair;
+  unsigned long long m = 0;
+  for (long k = threadIdx.x; k < npair; k += blockDim.x) {
+    const unsigned long long v = absbits(b[k]);
+    m = v > m ? v : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
+    mx[L] = m;
+    ex[L] = exp_of_maxbits(m);
+  }
+}
+
+// Pass 2: the stored tiles, one thread per element in storage order (plane by plane: tile, K
+// block of 16, row, column), digits relative to 2^e(L).
+__global__ void __launch_bounds__(256)
+k_bpacked_tiles(const double* __restrict__ Bp, long npair, int T, const int* __restrict__ ex,
+                Planes P, long total) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int c = (int)(i & 15), row = (int)((i >> 4) & 127), kk = (int)((i >> 11) & 7);
+  const long tt = i >> 14;              // tile index L T + t
+  const long L = tt / T;
+  const int t = (int)(tt - L * T);
+  int I = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);   // t = I (I + 1) / 2 + J, J <= I
+  while ((I + 1) * (I + 2) / 2 <= t) ++I;
+  while (I * (I + 1) / 2 > t) --I;
+  const int J = t - I * (I + 1) / 2;
+  const long mu = 128L * I + row, nu = 128L * J + 16 * kk + c;
+  const long hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
+  __nv_bfloat16 d[NDIG];
+  digits_of(Bp[L * npair + hi * (hi + 1) / 2 + lo], ex[L], d);
+  const long o = (tt * 8 + kk) * (128L * BK) + row * BK + c;
+#pragma unroll
+  for (int s = 0; s < NDIG; ++s) P.p[s * P.plane + o] = d[s];
+}
+
+// Pass 3: the ragged rows mu = n1 + j (rows (L, j) of all X r, then zero padding rows), every
+// K block of the layout (zero digits for nu >= n), in the K-blocked storage order.
+__global__ void __launch_bounds__(256)
+k_bpacked_ragged(const double* __restrict__ Bp, long npair, int n, int n1, int r,
+                 const int* __restrict__ ex, Planes P, long live_rows) {
+  const long kend = P.nkb * BK;
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= P.Rpad * kend) return;
+  const long kb = i / (P.Rpad * BK), rem = i - kb * (P.Rpad * BK);
+  const long row = rem / BK, k = kb * BK + (rem - row * BK);
+  double x = 0.0;
+  int e = 0;
+  if (row < live_rows) {
+    const long L = row / r, mu = n1 + (row - L * r);
+    e = ex[L];
+    if (k < n) {
+      const long hi = mu > k ? mu : k, lo = mu > k ? k : mu;
+      x = Bp[L * npair + hi * (hi + 1) / 2 + lo];
+    }
+  }
+  __nv_bfloat16 d[NDIG];
+  digits_of(x, e, d);
+#pragma unroll
+  for (int s = 0; s < NDIG; ++s) P.p[P.idx(s, row, k)] = d[s];
+}
+
 // Half-transformed rows (L,p) of Ht [R][n]: exponents and digit planes Hd (rows (L,p),
 // K = mu); the full transform reads them K-major and the projection MN-major (rows mu, K =
 // (L,p)), so one layout serves both.  Block: 16 rows r, 256 threads.  The row maxima are read
@@ -915,10 +1090,18 @@ static bool valid_bn(int bn) { return bn == 64 || bn == 96; }
 // (a repeated set from two threads is harmless).
 template <bool GROUPED, int FIXBN>
 static cudaError_t ozaki_attr() {
-  return cudaFuncSetAttribute(k_ozaki<OZ_BN, GROUPED, FIXBN>,
+  cudaError_t e = cudaFuncSetAttribute(k_ozaki<OZ_BN, GROUPED, FIXBN, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       OzTile<OZ_BN>::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_ozaki<OZ_BN, GROUPED, FIXBN, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               OzTile<OZ_BN>::SMEM_BYTES);
 }
+
+// Does the product need the instantiation with the packed-triangle logic (its A is the packed
+// form, or its rows are the ragged rows of that form, with one exponent per auxiliary index)?
+static inline bool needs_pack(const OzParams& p) { return p.a_pack || p.ea_perL; }
 
 static las_status ozaki_prepare() {
   static volatile int done[64];
@@ -1008,15 +1191,17 @@ las_status ozgroup_launch(const OzGroup* g, void* dev, cudaStream_t st) {
   int bn = g->probs[0].p.bn;   // one width for the whole launch, or 0: read per product
   for (const OzProblem& pr : g->probs)
     if (pr.p.bn != bn) bn = 0;
+  bool pack = false;
+  for (const OzProblem& pr : g->probs) pack |= needs_pack(pr.p);
   const OzProblem* probs = (const OzProblem*)dev;
   const int np = (int)g->probs.size();
   constexpr int SM = OzTile<OZ_BN>::SMEM_BYTES;
-  if (bn == 96)
-    k_ozaki<OZ_BN, true, 96><<<grid, NTHREADS, SM, st>>>(m0, m0, dummy, probs, np, g->tiles);
-  else if (bn == 64)
-    k_ozaki<OZ_BN, true, 64><<<grid, NTHREADS, SM, st>>>(m0, m0, dummy, probs, np, g->tiles);
-  else
-    k_ozaki<OZ_BN, true, 0><<<grid, NTHREADS, SM, st>>>(m0, m0, dummy, probs, np, g->tiles);
+  auto go = [&](auto kern) {
+    kern<<<grid, NTHREADS, SM, st>>>(m0, m0, m0, m0, dummy, probs, np, g->tiles);
+  };
+  if (bn == 96) pack ? go(k_ozaki<OZ_BN, true, 96, true>) : go(k_ozaki<OZ_BN, true, 96, false>);
+  else if (bn == 64) pack ? go(k_ozaki<OZ_BN, true, 64, true>) : go(k_ozaki<OZ_BN, true, 64, false>);
+  else pack ? go(k_ozaki<OZ_BN, true, 0, true>) : go(k_ozaki<OZ_BN, true, 0, false>);
   las_count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -1033,11 +1218,45 @@ las_status ozgroup_upload(const OzGroup* g, void* dev) {
   return LAS_OK;
 }
 
-las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const Planes& B,
-                      long b_row0, const int* eb, long N, long K, int ksplit, int mode,
-                      double* out, long ldc, long zstride, int ht_n, int ht_op, int* status,
-                      cudaStream_t st, int lower = 0, int bn = OZ_BN, int a_mn = 0) {
-  if (M <= 0 || N <= 0) return LAS_OK;
+// Launch one product (persistent: one CTA per SM), or record it into the group being recorded.
+static las_status ozaki_submit(OzProblem& pr, cudaStream_t st) {
+  const OzParams& p = pr.p;
+  const long tiles = p.tiles_z * p.ksplit;
+  if (g_record) {   // part of a grouped launch
+    pr.tile0 = g_record->tiles;
+    g_record->tiles += tiles;
+    g_record->probs.push_back(pr);
+    return LAS_OK;
+  }
+  dim3 grid((unsigned)std::min<long>(tiles, num_sms()), 1, 1);
+  constexpr int SM = OzTile<OZ_BN>::SMEM_BYTES;
+  auto go = [&](auto kern) {
+    kern<<<grid, NTHREADS, SM, st>>>(pr.tmA, pr.tmB, pr.tmA2, pr.tmA3, p, nullptr, 0, tiles);
+  };
+  const bool pack = needs_pack(p);
+  if (p.bn == 64) pack ? go(k_ozaki<OZ_BN, false, 64, true>) : go(k_ozaki<OZ_BN, false, 64, false>);
+  else pack ? go(k_ozaki<OZ_BN, false, 96, true>) : go(k_ozaki<OZ_BN, false, 96, false>);
+  las_count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    las_record_cuda_error(e, "k_ozaki launch", __FILE__, __LINE__);
+    return LAS_ERR_CUDA;
+  }
+  return LAS_OK;
+}
+
+// Fractional bits kept for the tail: |fixed-point sum| < 2^38 * (k per CTA) must fit 62 bits.
+static int tail_shift(int kb_per_split) {
+  int lgk = 0;
+  while ((1L << lgk) < (long)kb_per_split * BK) ++lgk;
+  return std::max(0, std::min(20, 61 - 14 - 8 * (NEXACT - 1) - lgk));
+}
+
+// The product's description (tensor maps and parameters), ready to be launched or recorded.
+static las_status ozaki_setup(OzProblem& pr, const Planes& A, long a_row0, const int* ea, long M,
+                              const Planes& B, long b_row0, const int* eb, long N, long K,
+                              int ksplit, int mode, double* out, long ldc, long zstride, int ht_n,
+                              int ht_op, int* status, int lower, int bn, int a_mn) {
   // a_mn: A's stored rows [a_row0, a_row0 + K) are the product's K, its stored K the rows M
   const bool a_ok = a_mn ? (a_row0 + K <= A.Rpad && M <= A.nkb * BK)
                          : (a_row0 + M <= A.Rpad && K <= A.nkb * BK);
@@ -1045,7 +1264,6 @@ las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const
     return LAS_ERR_INTERNAL;
   las_status s = ozaki_prepare();
   if (s != LAS_OK) return s;
-  OzProblem pr;
   memset(&pr, 0, sizeof(pr));
   if ((s = a_mn ? make_plane_map_mn(&pr.tmA, A) : make_plane_map(&pr.tmA, A, BM)) != LAS_OK)
     return s;
@@ -1071,35 +1289,89 @@ las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const
   p.zstride = zstride;
   p.ht_n = ht_n;
   p.ht_op = ht_op;
+  p.ht_rows = ht_n;
+  p.ht_mu0 = 0;
   p.lower = lower;
   p.tiles_z = ozaki_tiles(M, N, lower, bn);
-  // fractional bits kept for the tail: |fixed-point sum| < 2^38 * (k per CTA) must fit 62 bits
-  int lgk = 0;
-  while ((1L << lgk) < (long)p.kb_per_split * BK) ++lgk;
-  p.sh = std::max(0, std::min(20, 61 - 14 - 8 * (NEXACT - 1) - lgk));
+  p.sh = tail_shift(p.kb_per_split);
   p.bn = bn;
   p.a_mn = a_mn;
   p.status = status;
-  const long tiles = p.tiles_z * ksplit;
-  if (g_record) {   // part of a grouped launch
-    pr.tile0 = g_record->tiles;
-    g_record->tiles += tiles;
-    g_record->probs.push_back(pr);
-    return LAS_OK;
-  }
-  dim3 grid((unsigned)std::min<long>(tiles, num_sms()), 1, 1);   // persistent: one CTA per SM
-  constexpr int SM = OzTile<OZ_BN>::SMEM_BYTES;
-  if (bn == 64)
-    k_ozaki<OZ_BN, false, 64><<<grid, NTHREADS, SM, st>>>(pr.tmA, pr.tmB, p, nullptr, 0, tiles);
-  else
-    k_ozaki<OZ_BN, false, 96><<<grid, NTHREADS, SM, st>>>(pr.tmA, pr.tmB, p, nullptr, 0, tiles);
-  las_count_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    las_record_cuda_error(e, "k_ozaki launch", __FILE__, __LINE__);
-    return LAS_ERR_CUDA;
-  }
   return LAS_OK;
+}
+
+las_status ozaki_gemm(const Planes& A, long a_row0, const int* ea, long M, const Planes& B,
+                      long b_row0, const int* eb, long N, long K, int ksplit, int mode,
+                      double* out, long ldc, long zstride, int ht_n, int ht_op, int* status,
+                      cudaStream_t st, int lower = 0, int bn = OZ_BN, int a_mn = 0) {
+  if (M <= 0 || N <= 0) return LAS_OK;
+  OzProblem pr;
+  las_status s = ozaki_setup(pr, A, a_row0, ea, M, B, b_row0, eb, N, K, ksplit, mode, out, ldc,
+                             zstride, ht_n, ht_op, status, lower, bn, a_mn);
+  return s == LAS_OK ? ozaki_submit(pr, st) : s;
+}
+
+// out[L][p][mu] (the Ht layout, ht_op columns per L) = sum_nu b^L(mu, nu) X(nu, p) for the
+// auxiliary rows [l0, l0 + nL) of packed-triangle B and the N columns p of X whose digit planes
+// (rows p, K = nu) start at row x_row0 of Xd (column exponents xexp).  Two products: the full
+// 128-row blocks of every b^L from the stored tiles, and the ragged rows mu >= n1.
+static las_status bpacked_half(const BPacked& b, int l0, int nL, const Planes& Xd, long x_row0,
+                               const int* xexp, long N, double* out, int ht_op, int* status,
+                               cudaStream_t st, int bn) {
+  if (nL <= 0 || N <= 0) return LAS_OK;
+  if (l0 < 0 || l0 + nL > b.X || x_row0 + N > Xd.Rpad || b.n > Xd.nkb * BK || !valid_bn(bn))
+    return LAS_ERR_INTERNAL;
+  las_status rc = ozaki_prepare();
+  if (rc != LAS_OK) return rc;
+  if (b.nb1 > 0) {
+    const long M = (long)nL * b.n1;
+    if (M > 0x7FFFFFFFL) return LAS_ERR_UNSUPPORTED;
+    OzProblem pr;
+    memset(&pr, 0, sizeof(pr));
+    if ((rc = make_plane_map(&pr.tmA, b.tiles, BM)) != LAS_OK) return rc;
+    if ((rc = make_plane_map_mn(&pr.tmA2, b.tiles)) != LAS_OK) return rc;
+    if (b.r > 0 && (rc = make_plane_map_mn(&pr.tmA3, b.rag)) != LAS_OK) return rc;
+    if ((rc = make_plane_map(&pr.tmB, Xd, bn)) != LAS_OK) return rc;
+    OzParams& p = pr.p;
+    p.M = (int)M;
+    p.N = (int)N;
+    p.a_rpad = BM;
+    p.b_rpad = (int)Xd.Rpad;
+    p.b_row0 = (int)x_row0;
+    p.kb_total = (b.n + BK - 1) / BK;
+    p.kb_per_split = p.kb_total;
+    p.ksplit = 1;
+    p.ea = b.exp + l0;
+    p.eb = xexp;
+    p.out = out;
+    p.mode = 1;
+    p.ht_n = b.n;
+    p.ht_op = ht_op;
+    p.ht_rows = b.n1;
+    p.ht_mu0 = 0;
+    p.ea_perL = 1;
+    p.tiles_z = ozaki_tiles(M, N, 0, bn);
+    p.sh = tail_shift(p.kb_per_split);
+    p.bn = bn;
+    p.a_pack = 1;
+    p.pk_nb1 = b.nb1;
+    p.pk_T = b.T;
+    p.pk_r = b.r;
+    p.pk_L0 = l0;
+    p.status = status;
+    if ((rc = ozaki_submit(pr, st)) != LAS_OK) return rc;
+  }
+  if (b.r > 0) {
+    OzProblem pr;
+    rc = ozaki_setup(pr, b.rag, (long)l0 * b.r, b.exp + l0, (long)nL * b.r, Xd, x_row0, xexp, N,
+                     b.n, 1, 1, out, 0, 0, b.n, ht_op, status, 0, bn, 0);
+    if (rc != LAS_OK) return rc;
+    pr.p.ht_rows = b.r;
+    pr.p.ht_mu0 = b.n1;
+    pr.p.ea_perL = 1;
+    rc = ozaki_submit(pr, st);
+  }
+  return rc;
 }
 
 // live_only: only rows < R and the K blocks that hold K are written (planes whose padding rows
@@ -1140,8 +1412,10 @@ static las_status slice_rows(Acc acc, const Planes& P, int* ex, cudaStream_t st,
 
 struct SplitState {
   int n, X, op, Lc;
-  Planes Bdig;           // rows (L, mu) of all X*n, K = nu
-  int* Bexp;             // [X*n]
+  int packed;            // layout of the Cholesky vectors' digit planes:
+  Planes Bdig;           //   0: full rows (L, mu) of all X*n, K = nu, exponent per row
+  int* Bexp;             //      [X*n]
+  BPacked Bpk;           //   1: packed-triangle tiles, exponent per L
   Planes Cdig;           // rows p of C_occ^T, K = nu
   int* Cexp;             // [op]
   Planes Hdig;           // rows (L, p) of a chunk, K = mu
@@ -1174,7 +1448,9 @@ struct SplitState {
 static void split_free(SplitState* s) {
   if (s->Mpblob) cudaFree(s->Mpblob);
   if (s->tblob) cudaFree(s->tblob);
-  void* ptrs[] = {s->Bdig.p, s->Bexp, s->Cdig.p, s->Cexp, s->Hdig.p, s->Hexp, s->HdigT.p,
+  void* ptrs[] = {s->Bdig.p, s->Bexp, s->Bpk.tiles.p, s->Bpk.rag.p, s->Bpk.exp, s->Bpk.mx,
+                  s->Cdig.p, s->Cexp,
+                  s->Hdig.p, s->Hexp, s->HdigT.p,
                   s->Wdig.p, s->Wexp, s->part, s->mx, s->hdig.p, s->hexp, s->hcdig.p, s->hcexp};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -1186,7 +1462,7 @@ size_t split_bytes_per_aux(int n, int op) {
 }
 
 las_status split_create(SplitState** out, int n, int X, int op, int Lc, const double* Bp,
-                        int* status, cudaStream_t st, size_t* bytes) {
+                        int packed, int* status, cudaStream_t st, size_t* bytes) {
   *out = nullptr;
   if (!encode_fn()) return LAS_ERR_UNSUPPORTED;
   SplitState* s = (SplitState*)calloc(1, sizeof(SplitState));
@@ -1218,10 +1494,34 @@ las_status split_create(SplitState** out, int n, int X, int op, int Lc, const do
     }
     total += b;
   };
-  const long XN = (long)X * n, R = (long)Lc * op;
+  const long R = (long)Lc * op;
   void* q = nullptr;
-  A(&q, planes_bytes(XN, n));        s->Bdig = make_planes(q, XN, n);   q = nullptr;
-  A((void**)&s->Bexp, (size_t)XN * 4);
+  s->packed = packed != 0;
+  BPacked& bp = s->Bpk;
+  bp = bpacked_geometry(n, X);
+  if (!s->packed) {
+    A(&q, planes_bytes((long)X * n, n));
+    s->Bdig = make_planes(q, (long)X * n, n);
+    q = nullptr;
+    A((void**)&s->Bexp, (size_t)X * n * 4);
+  } else {
+  if (bp.nb1 > 0) {
+    A(&q, bpacked_tile_bytes(bp));
+    bp.tiles.p = (__nv_bfloat16*)q;
+    bp.tiles.R = bp.tiles.Rpad = 128;
+    bp.tiles.nkb = 8L * X * bp.T;
+    bp.tiles.K = bp.tiles.nkb * BK;
+    bp.tiles.plane = bp.tiles.nkb * 128 * BK;
+    q = nullptr;
+  }
+  if (bp.r > 0) {
+    A(&q, planes_bytes((long)X * bp.r, n));
+    bp.rag = make_planes(q, (long)X * bp.r, n);
+    q = nullptr;
+  }
+  A((void**)&bp.exp, (size_t)X * 4);
+  A((void**)&bp.mx, (size_t)X * 8);
+  }
   A(&q, planes_bytes(op, n));        s->Cdig = make_planes(q, op, n);   q = nullptr;
   A((void**)&s->Cexp, (size_t)op * 4);
   A(&q, planes_bytes(R, n));         s->Hdig = make_planes(q, R, n);    q = nullptr;
@@ -1249,10 +1549,32 @@ las_status split_create(SplitState** out, int n, int X, int op, int Lc, const do
       rc = LAS_ERR_CUDA;
     }
   }
-  if (rc == LAS_OK) {
+  if (rc == LAS_OK && !s->packed) {
     // one-time digit planes of the Cholesky vectors: rows (L, mu), K = nu
     RowsPacked acc{Bp, (long)n * (n + 1) / 2, n};
     rc = slice_rows(acc, s->Bdig, s->Bexp, st);
+  } else if (rc == LAS_OK) {
+    // one-time packed-triangle digit planes of the Cholesky vectors, one exponent per L
+    const long npair = (long)n * (n + 1) / 2;
+    k_bpacked_max<<<(unsigned)X, 256, 0, st>>>(Bp, npair, bp.mx, bp.exp);
+    las_count_launch();
+    if (bp.nb1 > 0) {
+      const long total = 8L * X * bp.T * 128 * BK;
+      k_bpacked_tiles<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(Bp, npair, bp.T, bp.exp,
+                                                                        bp.tiles, total);
+      las_count_launch();
+    }
+    if (bp.r > 0) {
+      const long total = bp.rag.Rpad * bp.rag.nkb * BK;
+      k_bpacked_ragged<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+          Bp, npair, n, bp.n1, bp.r, bp.exp, bp.rag, (long)X * bp.r);
+      las_count_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      las_record_cuda_error(e, "packed digit planes of B", __FILE__, __LINE__);
+      rc = LAS_ERR_CUDA;
+    }
   }
   if (rc != LAS_OK) {
     split_free(s);
@@ -1285,6 +1607,18 @@ las_status split_set_tile(SplitState* s, int kind, int bn) {
   return LAS_OK;
 }
 void split_set_ksplit(SplitState* s, int ks) { s->ks = std::max(1, std::min(ks, s->ksplit6)); }
+
+// The half-transform-shaped products of the Cholesky vectors, in either digit layout:
+// out[L][p][mu] (ht_op columns per L) = sum_nu b^L(mu, nu) X(nu, p) for L in [l0, l0 + nL), X
+// given by the digit planes of its transpose (rows p from x_row0, K = nu; exponents xexp).
+static las_status b_half(const SplitState* s, int l0, int nL, const Planes& Xd, long x_row0,
+                         const int* xexp, long N, double* out, int ht_op, cudaStream_t st,
+                         int bn) {
+  if (s->packed)
+    return bpacked_half(s->Bpk, l0, nL, Xd, x_row0, xexp, N, out, ht_op, s->status, st, bn);
+  return ozaki_gemm(s->Bdig, (long)l0 * s->n, s->Bexp + (long)l0 * s->n, (long)nL * s->n, Xd,
+                    x_row0, xexp, N, s->n, 1, 1, out, 0, 0, s->n, ht_op, s->status, st, 0, bn);
+}
 
 las_status split_prepare_C(SplitState* s, const double* Cocc, cudaStream_t st) {
   // rows p of C_occ^T (K = nu): element (p, nu) = Cocc[nu*op + p]
@@ -1326,9 +1660,7 @@ las_status split_tangent_prepare(SplitState* s, const double* dCocc, cudaStream_
 
 // dH = b^L dC_occ for the chunk's aux rows (Ht layout [nL][op][n])
 las_status split_tangent_half(SplitState* s, int l0, int nL, double* dHt, cudaStream_t st) {
-  return ozaki_gemm(s->Bdig, (long)l0 * s->n, s->Bexp + (long)l0 * s->n, (long)nL * s->n,
-                    s->dCdig, 0, s->dCexp, s->op, s->n, 1, 1, dHt, 0, 0, s->n, s->op, s->status,
-                    st, 0, s->bn[SPLIT_HALF]);
+  return b_half(s, l0, nL, s->dCdig, 0, s->dCexp, s->op, dHt, s->op, st, s->bn[SPLIT_HALF]);
 }
 
 // After split_full of the chunk: X[(L,p)][q] = sum_mu H_L(mu,p) dC(mu,q) (so that dT_L = X_L +
@@ -1418,21 +1750,16 @@ las_status split_lpu(SplitState* s, int nL, const double* Ht, int c, int a, cons
 // quarters of a 96-column one.  Not while products are recorded for a grouped launch, which would
 // then mix tile widths.
 las_status split_half(SplitState* s, int l0, int nL, int oc, double* Ht, cudaStream_t st) {
-  const long rows = (long)nL * s->n;
   if (oc < 1 || oc > s->op) return LAS_ERR_INTERNAL;
   const int bn = s->bn[SPLIT_HALF];
   const int whole = oc / 96 * 96, rest = oc - whole;
   if (bn == 96 && whole > 0 && rest > 0 && rest <= 64 && !g_record) {
-    las_status rc = ozaki_gemm(s->Bdig, (long)l0 * s->n, s->Bexp + (long)l0 * s->n, rows,
-                               s->Cdig, 0, s->Cexp, whole, s->n, 1, 1, Ht, 0, 0, s->n, oc,
-                               s->status, st, 0, 96);
+    las_status rc = b_half(s, l0, nL, s->Cdig, 0, s->Cexp, whole, Ht, oc, st, 96);
     if (rc != LAS_OK) return rc;
-    return ozaki_gemm(s->Bdig, (long)l0 * s->n, s->Bexp + (long)l0 * s->n, rows, s->Cdig, whole,
-                      s->Cexp + whole, rest, s->n, 1, 1, Ht + (size_t)whole * s->n, 0, 0, s->n,
-                      oc, s->status, st, 0, 64);
+    return b_half(s, l0, nL, s->Cdig, whole, s->Cexp + whole, rest, Ht + (size_t)whole * s->n,
+                  oc, st, 64);
   }
-  return ozaki_gemm(s->Bdig, (long)l0 * s->n, s->Bexp + (long)l0 * s->n, rows, s->Cdig, 0,
-                    s->Cexp, oc, s->n, 1, 1, Ht, 0, 0, s->n, oc, s->status, st, 0, bn);
+  return b_half(s, l0, nL, s->Cdig, 0, s->Cexp, oc, Ht, oc, st, bn);
 }
 
 las_status split_full(SplitState* s, int nL, const double* Ht, double* T, cudaStream_t st) {
@@ -1708,8 +2035,7 @@ las_status frag_split_chunk(SplitState* s, FragSplit* f, int l0, int nL, double*
   const long n2 = (long)nmo * nmo, R1 = (long)nL * nmo;
   if (nL < 1 || nL > f->Lc || ma > f->ma) return LAS_ERR_INTERNAL;
   // Eq. ao2mo_1: H[L][p][e2] = sum_e1 b^L(e2, e1) M[e1][p]
-  las_status rc = ozaki_gemm(s->Bdig, (long)l0 * n, s->Bexp + (long)l0 * n, (long)nL * n, f->Mdig,
-                             0, f->Mexp, nmo, n, 1, 1, H, 0, 0, n, nmo, s->status, st);
+  las_status rc = b_half(s, l0, nL, f->Mdig, 0, f->Mexp, nmo, H, nmo, st, OZ_BN);
   // Eq. ao2mo_2: T[L][p][q] = sum_e H[L][p][e] M[e][q]
   Planes Hd = f->Hd;
   Hd.R = R1;

@@ -4,10 +4,12 @@
 
 struct SplitState;
 
-// Builds the one-time digit planes of the packed Cholesky vectors.  Device errors (timeouts of
-// bounded waits) are recorded in *status.
+// Builds the one-time digit planes of the packed Cholesky vectors: full rows (L, mu) with one
+// exponent per row (packed = 0), or the packed-triangle tiles with one exponent per auxiliary
+// index (packed = 1, about 0.55 of the bytes).  Device errors (timeouts of bounded waits) are
+// recorded in *status.
 las_status split_create(SplitState** s, int n, int X, int op, int Lc, const double* Bp,
-                        int* status, cudaStream_t st, size_t* bytes);
+                        int packed, int* status, cudaStream_t st, size_t* bytes);
 // Device bytes per auxiliary index of the per-evaluation digit workspace.
 size_t split_bytes_per_aux(int n, int op);
 // Row exponents of the current chunk's half-transformed rows (L, p): the per-aux kernel scales

@@ -16,7 +16,10 @@ LIB_PATH = os.path.join(HERE, "liblasdf.so")
 
 LAS_FP64 = 0
 LAS_SPLIT_BF16 = 1
-PRECISIONS = {"fp64": LAS_FP64, "split": LAS_SPLIT_BF16, "split_bf16": LAS_SPLIT_BF16}
+LAS_SPLIT_BF16_PACKED = 2
+# "split_packed": split precision over packed-triangle digit planes of B (less memory)
+PRECISIONS = {"fp64": LAS_FP64, "split": LAS_SPLIT_BF16, "split_bf16": LAS_SPLIT_BF16,
+              "split_packed": LAS_SPLIT_BF16_PACKED}
 
 EXPORTS = ["las_create", "las_destroy", "las_set_stream", "las_sync", "las_device_bytes",
            "las_df_transform", "las_df_jk", "las_energy", "las_energy_grad",

@@ -39,7 +39,7 @@ int main(void) {
   nact[1] = 0;                                      /* an empty fragment */
   CHECK(7, las_create(&ctx, &d, dummy, LAS_FP64, 0, NULL) == LAS_ERR_ARG);
   nact[1] = 2;
-  CHECK(8, las_create(&ctx, &d, dummy, (las_precision)2, 0, NULL) == LAS_ERR_ARG);
+  CHECK(8, las_create(&ctx, &d, dummy, (las_precision)3, 0, NULL) == LAS_ERR_ARG);
   d.ncore = 0; d.nfrag = 0;                         /* nothing occupied */
   CHECK(9, las_create(&ctx, &d, dummy, LAS_FP64, 0, NULL) == LAS_ERR_ARG);
 

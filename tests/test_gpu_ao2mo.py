@@ -26,7 +26,8 @@ def _case(nao, naux, seed):
     return s, M
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("split", 1e-10)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("split", 1e-10),
+                                           ("split_packed", 1e-10)])
 @pytest.mark.parametrize("nao,naux,a0,ma,seed", CASES)
 def test_frag_ao2mo(precision, tol, nao, naux, a0, ma, seed):
     torch_cuda()

@@ -38,6 +38,7 @@ def test_orbital_hvp_small(precision, tol, name):
     _check(SMALL[name](), precision, tol, seed=21)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("split", 1e-9)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("split", 1e-9),
+                                           ("split_packed", 1e-9)])
 def test_orbital_hvp_nao400(precision, tol):
     _check(workload_system("nao400"), precision, tol, seed=22)

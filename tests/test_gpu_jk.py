@@ -10,7 +10,8 @@ from oracle import las_oracle as O
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("split", 1e-11)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("split", 1e-11),
+                                           ("split_packed", 1e-11)])
 @pytest.mark.parametrize("r", [1, 12, 30])
 def test_df_jk_density(precision, tol, r):
     torch_cuda()

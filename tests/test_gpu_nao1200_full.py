@@ -4,7 +4,8 @@ times (default workspace, every auxiliary row in one context).
 * The oracle evaluates the same system over all 4800 auxiliary functions (the full sums over P
   of Eqs. J_1-K_2 and ppaa; a few minutes on the host cores), and both precisions are compared
   with it element by element at the stated bars: FP64 |dE| <= 1e-10 |E| and max|d dE/dC| <= 1e-9;
-  split |dE| <= 1e-8 Eh and max|d dE/dC| <= 1e-8.
+  split |dE| <= 1e-8 Eh and max|d dE/dC| <= 1e-8, for both digit layouts of B (full rows, and
+  the packed triangle with one exponent per auxiliary function).
 * The energy and gradients are sums over L plus an h-linear term, so the whole-index context,
   whose B offsets pass 2^31 elements, must equal the sum of two contexts over the halves of the
   auxiliary index (each below 2^31 elements), the second one passed h = 0.  Both sides are split
@@ -51,7 +52,7 @@ def _eval(s, B, naux, precision, C, h, dm1s, dm2):
         las.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "split"])
+@pytest.mark.parametrize("precision", ["fp64", "split", "split_packed"])
 def test_nao1200_full_size_against_oracle(full, precision):
     s, B, ref = full
     assert B.numel() > 2**31

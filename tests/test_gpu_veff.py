@@ -30,7 +30,8 @@ def _spin_blocks(dm1s, sigma):
     return g
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("split", 1e-11)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("split", 1e-11),
+                                           ("split_packed", 1e-11)])
 def test_veff_embedding_potential(precision, tol):
     torch_cuda()
     built()
