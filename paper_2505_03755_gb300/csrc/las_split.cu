@@ -462,38 +462,36 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
       }
       long pend0 = 0;     // first deferred stage (global index) and count
       int npend = 0, pend_i0 = 0;
-      for (int i = 0; i < nkb; ++i, ++gs) {
+      // One stage: wait for its data, issue its tail MMAs, then the exact-group MMAs of the
+      // deferred stages and its own unless they are deferred again (never at the end of a chunk
+      // or of a phase: flush).  amn is the stage's A orientation.  False when a wait ran out.
+      auto stage = [&](int i, bool amn, bool flush) -> bool {
         const int st = (int)(gs % NSTAGE);
         if (!sm100::mbar_wait(&full[st], (uint32_t)(gs / NSTAGE) & 1, abort_flag, p.status,
-                              LAS_ERR_TIMEOUT)) {
-          ok = false;
-          break;
-        }
+                              LAS_ERR_TIMEOUT))
+          return false;
         sm100::tc_fence_after();
         {
           const uint32_t sa = sm100::smem_u32(smem + st * T::STAGE_BYTES);
           const uint32_t sb = sa + A_BYTES;
-          const bool amn = PACK ? (pack ? (cur.kb0 + i >= kb_mn) : amn_tile) : amn_tile;
           // tail: the 11 products of groups 4 and 5 into the one tail accumulator
           if (bn == 64) mma_tail<64>(tmem + T::TAIL_COL, sa, sb, i == 0, amn);
           else mma_tail<96>(tmem + T::TAIL_COL, sa, sb, i == 0, amn);
         }
         const bool last_in_chunk = (i % CHUNK) == CHUNK - 1 || i == nkb - 1;
         if (need_acce) {
-          if (!last_in_chunk && npend < NSTAGE - 1 &&
+          if (!last_in_chunk && !flush && npend < NSTAGE - 1 &&
               !sm100::mbar_test_wait(acce, (uint32_t)(gc - 1) & 1)) {
             if (npend == 0) {
               pend0 = gs;
               pend_i0 = i;
             }
             ++npend;
-            continue;   // defer this stage's exact-group MMAs
+            return true;   // defer this stage's exact-group MMAs
           }
           if (!sm100::mbar_wait(acce, (uint32_t)(gc - 1) & 1, abort_flag, p.status,
-                                LAS_ERR_TIMEOUT)) {
-            ok = false;
-            break;
-          }
+                                LAS_ERR_TIMEOUT))
+            return false;
           sm100::tc_fence_after();
           need_acce = false;
         }
@@ -511,7 +509,6 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
           const bool first_in_chunk = (i2 % CHUNK) == 0;
           const uint32_t sa = sm100::smem_u32(smem + st2 * T::STAGE_BYTES);
           const uint32_t sb = sa + A_BYTES;
-          const bool amn = PACK ? (pack ? (cur.kb0 + i2 >= kb_mn) : amn_tile) : amn_tile;
           if (bn == 64) mma_exact<64>(tmem, sa, sb, first_in_chunk, amn);
           else mma_exact<96>(tmem, sa, sb, first_in_chunk, amn);
           sm100::mma_commit(&empty[st2]);
@@ -522,7 +519,75 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
           ++gc;
           need_acce = true;   // the next chunk's exact MMAs wait for this chunk's drain
         }
+        return true;
+      };
+      if constexpr (PACK) {
+        // packed-triangle A: the K-major stages (up to the diagonal block) and the MN-major
+        // ones as two loops, each of one orientation; the first leaves nothing deferred
+        const int isplit = pack ? min(nkb, max(0, kb_mn - cur.kb0)) : nkb;
+        const bool amn0 = pack ? false : amn_tile;
+        for (int i = 0; i < isplit && ok; ++i, ++gs) ok = stage(i, amn0, i == isplit - 1);
+        for (int i = isplit; i < nkb && ok; ++i, ++gs) ok = stage(i, true, false);
+      } else {
+        // the same per stage as `stage`, written out: one orientation for the whole tile
+        const bool amn = amn_tile;
+        for (int i = 0; i < nkb; ++i, ++gs) {
+          const int st = (int)(gs % NSTAGE);
+          if (!sm100::mbar_wait(&full[st], (uint32_t)(gs / NSTAGE) & 1, abort_flag, p.status,
+                                LAS_ERR_TIMEOUT)) {
+            ok = false;
+            break;
+          }
+          sm100::tc_fence_after();
+          {
+            const uint32_t sa = sm100::smem_u32(smem + st * T::STAGE_BYTES);
+            const uint32_t sb = sa + A_BYTES;
+            if (bn == 64) mma_tail<64>(tmem + T::TAIL_COL, sa, sb, i == 0, amn);
+            else mma_tail<96>(tmem + T::TAIL_COL, sa, sb, i == 0, amn);
+          }
+          const bool last_in_chunk = (i % CHUNK) == CHUNK - 1 || i == nkb - 1;
+          if (need_acce) {
+            if (!last_in_chunk && npend < NSTAGE - 1 &&
+                !sm100::mbar_test_wait(acce, (uint32_t)(gc - 1) & 1)) {
+              if (npend == 0) {
+                pend0 = gs;
+                pend_i0 = i;
+              }
+              ++npend;
+              continue;   // defer this stage's exact-group MMAs
+            }
+            if (!sm100::mbar_wait(acce, (uint32_t)(gc - 1) & 1, abort_flag, p.status,
+                                  LAS_ERR_TIMEOUT)) {
+              ok = false;
+              break;
+            }
+            sm100::tc_fence_after();
+            need_acce = false;
+          }
+          if (npend == 0) {
+            pend0 = gs;
+            pend_i0 = i;
+          }
+          for (int j = 0; j <= npend; ++j) {
+            const long g2 = pend0 + j;
+            const int i2 = pend_i0 + j;
+            const int st2 = (int)(g2 % NSTAGE);
+            const bool first_in_chunk = (i2 % CHUNK) == 0;
+            const uint32_t sa = sm100::smem_u32(smem + st2 * T::STAGE_BYTES);
+            const uint32_t sb = sa + A_BYTES;
+            if (bn == 64) mma_exact<64>(tmem, sa, sb, first_in_chunk, amn);
+            else mma_exact<96>(tmem, sa, sb, first_in_chunk, amn);
+            sm100::mma_commit(&empty[st2]);
+          }
+          npend = 0;
+          if (last_in_chunk) {
+            sm100::mma_commit(accf);
+            ++gc;
+            need_acce = true;
+          }
+        }
       }
+      if (!ok) break;
       ++tcount;
     }
     // make sure no MMA is still writing TMEM when the CTA tears down
