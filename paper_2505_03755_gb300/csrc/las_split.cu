@@ -23,6 +23,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "las_split.cuh"
@@ -319,7 +320,7 @@ __device__ __forceinline__ void mma_exact(uint32_t tmem, uint32_t sa, uint32_t s
 // widths share a grouped launch (each tile then reads its product's width).  PACK: the launch
 // may hold products whose A is the packed-triangle form of the Cholesky vectors (a_pack); the
 // other instantiations leave that logic out of the issuing and loading threads entirely.
-template <int BN, bool GROUPED, int FIXBN, bool PACK>
+template <int BN, bool GROUPED, int FIXBN, bool PACK, int AMN = 2>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
         const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmA3,
@@ -465,7 +466,8 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
       // One stage: wait for its data, issue its tail MMAs, then the exact-group MMAs of the
       // deferred stages and its own unless they are deferred again (never at the end of a chunk
       // or of a phase: flush).  amn is the stage's A orientation.  False when a wait ran out.
-      auto stage = [&](int i, bool amn, bool flush) -> bool {
+      auto stage = [&](auto amn_c, int i, bool flush) -> bool {
+        constexpr bool amn = decltype(amn_c)::value;   // the orientation as a constant
         const int st = (int)(gs % NSTAGE);
         if (!sm100::mbar_wait(&full[st], (uint32_t)(gs / NSTAGE) & 1, abort_flag, p.status,
                               LAS_ERR_TIMEOUT))
@@ -522,15 +524,22 @@ k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
         return true;
       };
       if constexpr (PACK) {
-        // packed-triangle A: the K-major stages (up to the diagonal block) and the MN-major
-        // ones as two loops, each of one orientation; the first leaves nothing deferred
-        const int isplit = pack ? min(nkb, max(0, kb_mn - cur.kb0)) : nkb;
-        const bool amn0 = pack ? false : amn_tile;
-        for (int i = 0; i < isplit && ok; ++i, ++gs) ok = stage(i, amn0, i == isplit - 1);
-        for (int i = isplit; i < nkb && ok; ++i, ++gs) ok = stage(i, true, false);
+        using K_MAJOR = std::integral_constant<bool, false>;
+        using MN_MAJOR = std::integral_constant<bool, true>;
+        if (pack) {
+          // packed-triangle A: the K-major stages (up to the diagonal block) and the MN-major
+          // ones as two loops, each of one orientation; the first leaves nothing deferred
+          const int isplit = min(nkb, max(0, kb_mn - cur.kb0));
+          for (int i = 0; i < isplit && ok; ++i, ++gs) ok = stage(K_MAJOR(), i, i == isplit - 1);
+          for (int i = isplit; i < nkb && ok; ++i, ++gs) ok = stage(MN_MAJOR(), i, false);
+        } else if (amn_tile) {
+          for (int i = 0; i < nkb && ok; ++i, ++gs) ok = stage(MN_MAJOR(), i, false);
+        } else {
+          for (int i = 0; i < nkb && ok; ++i, ++gs) ok = stage(K_MAJOR(), i, false);
+        }
       } else {
         // the same per stage as `stage`, written out: one orientation for the whole tile
-        const bool amn = amn_tile;
+        const bool amn = AMN == 2 ? amn_tile : AMN == 1;
         for (int i = 0; i < nkb; ++i, ++gs) {
           const int st = (int)(gs % NSTAGE);
           if (!sm100::mbar_wait(&full[st], (uint32_t)(gs / NSTAGE) & 1, abort_flag, p.status,
@@ -1159,6 +1168,15 @@ static cudaError_t ozaki_attr() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        OzTile<OZ_BN>::SMEM_BYTES);
   if (e != cudaSuccess) return e;
+  if constexpr (!GROUPED && FIXBN != 0) {
+    e = cudaFuncSetAttribute(k_ozaki<OZ_BN, GROUPED, FIXBN, false, 0>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, OzTile<OZ_BN>::SMEM_BYTES);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_ozaki<OZ_BN, GROUPED, FIXBN, false, 1>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               OzTile<OZ_BN>::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(k_ozaki<OZ_BN, GROUPED, FIXBN, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               OzTile<OZ_BN>::SMEM_BYTES);
@@ -1299,8 +1317,17 @@ static las_status ozaki_submit(OzProblem& pr, cudaStream_t st) {
     kern<<<grid, NTHREADS, SM, st>>>(pr.tmA, pr.tmB, pr.tmA2, pr.tmA3, p, nullptr, 0, tiles);
   };
   const bool pack = needs_pack(p);
-  if (p.bn == 64) pack ? go(k_ozaki<OZ_BN, false, 64, true>) : go(k_ozaki<OZ_BN, false, 64, false>);
-  else pack ? go(k_ozaki<OZ_BN, false, 96, true>) : go(k_ozaki<OZ_BN, false, 96, false>);
+  // full-row products take an instantiation with their A orientation as a compile-time constant
+  if (pack) {
+    if (p.bn == 64) go(k_ozaki<OZ_BN, false, 64, true>);
+    else go(k_ozaki<OZ_BN, false, 96, true>);
+  } else if (p.a_mn) {
+    if (p.bn == 64) go(k_ozaki<OZ_BN, false, 64, false, 1>);
+    else go(k_ozaki<OZ_BN, false, 96, false, 1>);
+  } else {
+    if (p.bn == 64) go(k_ozaki<OZ_BN, false, 64, false, 0>);
+    else go(k_ozaki<OZ_BN, false, 96, false, 0>);
+  }
   las_count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
