@@ -410,8 +410,8 @@ SPLIT_MODES = ("split", "split_packed")
 # evaluation by the rows processed (the traffic is proportional to the rows: digits of B read
 # once, H written once).  "split_packed" sums the two launches of that layout (the whole 128-row
 # blocks and the ragged rows).
-S1_TRAFFIC_PER_ROW = {"split": (3526925056 + 378429696) / (200 * 1200),
-                      "split_packed": (2046610944 + 354959104 + 141704448 + 1675008) / (200 * 1200)}
+S1_TRAFFIC_PER_ROW = {"split": (3527966208 + 378804224) / (200 * 1200),
+                      "split_packed": (2052677120 + 355101952 + 141710848 + 1297664) / (200 * 1200)}
 
 
 def roofline_for(prec, r, work, peaks, s):
