@@ -40,6 +40,11 @@ int main(void) {
   CHECK(7, las_create(&ctx, &d, dummy, LAS_FP64, 0, NULL) == LAS_ERR_ARG);
   nact[1] = 2;
   CHECK(8, las_create(&ctx, &d, dummy, (las_precision)3, 0, NULL) == LAS_ERR_ARG);
+  d.nmo = 5;                                        /* the packed layout validates the same */
+  CHECK(16, LAS_SPLIT_BF16_PACKED == 2 &&
+                las_create(&ctx, &d, dummy, LAS_SPLIT_BF16_PACKED, 0, NULL) == LAS_ERR_ARG &&
+                ctx == NULL);
+  d.nmo = 10;
   d.ncore = 0; d.nfrag = 0;                         /* nothing occupied */
   CHECK(9, las_create(&ctx, &d, dummy, LAS_FP64, 0, NULL) == LAS_ERR_ARG);
 
