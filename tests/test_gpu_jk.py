@@ -84,11 +84,13 @@ def test_df_jk_density_weight_edge_cases(precision, tol):
     las.close()
 
 
+@pytest.mark.parametrize("precision", ["split", "split_packed"])
 @pytest.mark.parametrize("r", [100, 150, 170])
-def test_split_df_jk_density_two_tile_widths(r):
+def test_split_df_jk_density_two_tile_widths(r, precision):
     """Density ranks past one 96-column tile: r = 100 and 150 run the half transform as a
     96-column product plus a 64-column product over the remaining columns (4 and 54 of them);
-    r = 170 leaves 74 and stays in 96-column tiles.  All against the oracle's JK."""
+    r = 170 leaves 74 and stays in 96-column tiles.  All against the oracle's JK, for both digit
+    layouts of B (180 AOs: one whole 128-row block and 52 ragged rows when packed)."""
     torch_cuda()
     built()
     from paper_2505_03755_gb300 import LasDF
@@ -98,7 +100,7 @@ def test_split_df_jk_density_two_tile_widths(r):
     w = rng.standard_normal(r)
     D = Cx @ np.diag(w) @ Cx.T
     (Jr,), (Kr,) = O.df_jk(s.Bp, s.nao, [D])
-    las = LasDF(dev(s.Bp), s.nao, s.naux, s.nmo, s.ncore, [], precision="split")
+    las = LasDF(dev(s.Bp), s.nao, s.naux, s.nmo, s.ncore, [], precision=precision)
     J, K = las.df_jk_density(dev(Cx), dev(w))
     las.sync()
     assert np.abs(J.cpu().numpy() - Jr).max() <= 1e-11 * np.abs(Jr).max()
