@@ -319,7 +319,10 @@ __device__ __forceinline__ void mma_exact(uint32_t tmem, uint32_t sa, uint32_t s
 // every product of the launch as a compile-time constant (64 or 96), or 0 when products of both
 // widths share a grouped launch (each tile then reads its product's width).  PACK: the launch
 // may hold products whose A is the packed-triangle form of the Cholesky vectors (a_pack); the
-// other instantiations leave that logic out of the issuing and loading threads entirely.
+// other instantiations leave that logic out of the issuing and loading threads entirely.  AMN:
+// the A orientation of the launch's products as a compile-time constant (0: K-major, 1:
+// MN-major), or 2 when each tile reads its product's; the issuing thread runs measurably faster
+// with a constant.
 template <int BN, bool GROUPED, int FIXBN, bool PACK, int AMN = 2>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
