@@ -5,8 +5,12 @@ One step = one full energy + dE/dC evaluation (every stage of the chain) over th
 synthetic, seeded Cholesky vectors (27.7 GB packed FP64, far larger than L2, so no L2 flush is
 needed between steps).  Prints ONE JSON line on rank 0.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision split|fp64|both]
+  python bench.py [--gpus N] [--steps K] [--warmup W]
+                  [--precision both|split_packed|split|fp64] [--batched-precision ...]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample of the workload
+
+The headline is the split mode over packed-triangle digit planes of B ("split_packed"); native
+FP64 and the split mode over full-row digit planes ("split") are timed beside it.
 
 Under torchrun (N > 1) the default (--partition aux) splits the one Nao=1200 system along the
 auxiliary index: each rank holds its block of rows of B and evaluates its share, and one NCCL

@@ -28,3 +28,30 @@ def test_reference_arm_json_line():
     # the step is a bounded sample of one evaluation: the line says so and its step time is
     # the measured one
     assert "value_projection" in d and d["ms_per_step"] < 60e3
+
+
+def test_roofline_of_both_split_layouts():
+    """The half transform's roofline entry for both digit layouts of B: digit-product flops over
+    the stage time against the sustained BF16 peak, and the measured per-row DRAM traffic scaled
+    to the workload's rows (the packed planes move about two thirds of the full-row bytes)."""
+    import sys
+    from types import SimpleNamespace
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import bench
+    s = SimpleNamespace(naux=4800, nao=1200)
+    work = bench.algorithmic_work(1200, 4800, 150, 40)
+    r = {"stage_ms": [42.0, 12.0, 3.0, 8.0, 0.2]}
+    peaks = {"bf16_tflops_sustained": 1728.1}
+    out = {k: bench.roofline_for(k, r, work, peaks, s) for k in ("split", "split_packed")}
+    for rf in out.values():
+        assert rf["bound"] == "tensor" and rf["unit"] == "TFLOP/s"
+        assert abs(rf["achieved"] - 21 * work["s1"] / 0.042 / 1e12) < 1e-6
+        assert abs(rf["frac"] - rf["achieved"] / 1728.1) < 1e-12
+        assert rf["traffic"] is not None
+    full, packed = out["split"]["traffic"], out["split_packed"]["traffic"]
+    # full rows: six BF16 planes of a 1200-long row (14.4 KB) plus 192 FP64 outputs, read and
+    # written once; packed: 45 tiles and 48 ragged rows per b^L, 0.55 of the digits
+    assert 0.95 * 5.76e6 * 15.9e3 < full < 1.1 * 5.76e6 * 15.9e3
+    assert 0.6 * full < packed < 0.7 * full
